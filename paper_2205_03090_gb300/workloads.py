@@ -1,0 +1,120 @@
+"""Seeded synthetic inputs for the flash workloads.
+
+This module draws random numbers only; it holds none of the method's
+arithmetic, so both the CUDA path and the CPU oracle can be fed from it.
+Every draw uses NumPy ``Generator(PCG64(seed))``.
+
+Workloads (sizes named by what they are):
+  * ``nc3_1e4``  -- 3 pseudo-components, 1e4 mixtures, z ~ Dirichlet(1)
+  * ``nc8_1e6``  -- 8 pseudo-components, 1e6 mixtures, z ~ Dirichlet(0.5)
+  * ``nc10_2phase_1e6`` -- 10 pseudo-components, T in [250, 450] K,
+    P in [2, 15] MPa, z ~ Dirichlet(1) (two-phase-biased conditions)
+Pseudo-components: Tc ~ U(150, 650) K sorted ascending, Pc ~ U(2, 5) MPa,
+omega ~ U(0, 0.5), symmetric k_ij ~ U(0, 0.1) with zero diagonal.  The paper's
+own case-study data are synthetic too (Sec. 2.4: LHS + Dirichlet draws);
+these draws stand in for them.  Compositions are floored at 1e-12 and
+renormalised so that ln z stays finite for both implementations.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+Z_FLOOR = 1e-12
+
+
+@dataclass
+class Components:
+    Tc: np.ndarray      # [nc] K
+    Pc: np.ndarray      # [nc] MPa
+    omega: np.ndarray   # [nc]
+    kij: np.ndarray     # [nc, nc] symmetric, zero diagonal
+
+    @property
+    def nc(self) -> int:
+        return int(self.Tc.shape[0])
+
+
+@dataclass
+class Conditions:
+    P: np.ndarray   # [n] MPa
+    T: np.ndarray   # [n] K
+    z: np.ndarray   # [nc, n] component-major, columns sum to 1
+
+    @property
+    def n(self) -> int:
+        return int(self.P.shape[0])
+
+
+def pseudo_components(nc: int, seed: int) -> Components:
+    g = np.random.Generator(np.random.PCG64(seed))
+    Tc = np.sort(g.uniform(150.0, 650.0, nc))
+    Pc = g.uniform(2.0, 5.0, nc)
+    om = g.uniform(0.0, 0.5, nc)
+    k = g.uniform(0.0, 0.1, (nc, nc))
+    k = np.triu(k, 1)
+    k = k + k.T
+    return Components(Tc, Pc, om, k)
+
+
+def dirichlet(g: np.random.Generator, alpha: float, nc: int, n: int) -> np.ndarray:
+    z = g.dirichlet(np.full(nc, alpha), size=n).T.copy()  # [nc, n]
+    z = np.maximum(z, Z_FLOOR)
+    z /= z.sum(axis=0, keepdims=True)
+    return np.ascontiguousarray(z)
+
+
+def conditions(nc: int, n: int, seed: int, T_range=(200.0, 600.0), P_range=(0.1, 20.0),
+               alpha: float = 1.0) -> Conditions:
+    g = np.random.Generator(np.random.PCG64(seed))
+    T = g.uniform(T_range[0], T_range[1], n)
+    P = g.uniform(P_range[0], P_range[1], n)
+    z = dirichlet(g, alpha, nc, n)
+    return Conditions(P, T, z)
+
+
+# Named workloads: (nc, n, component seed, condition seed, T range, P range, alpha)
+WORKLOADS = {
+    "nc3_1e4": dict(nc=3, n=10_000, comp_seed=0, cond_seed=0, T_range=(200.0, 600.0), P_range=(0.1, 20.0),
+                    alpha=1.0),
+    "nc8_1e6": dict(nc=8, n=1_000_000, comp_seed=0, cond_seed=1, T_range=(200.0, 600.0), P_range=(0.1, 20.0),
+                    alpha=0.5),
+    "nc10_2phase_1e6": dict(nc=10, n=1_000_000, comp_seed=0, cond_seed=3, T_range=(250.0, 450.0),
+                            P_range=(2.0, 15.0), alpha=1.0),
+    "nc10_2phase_1e7": dict(nc=10, n=10_000_000, comp_seed=0, cond_seed=4, T_range=(250.0, 450.0),
+                            P_range=(2.0, 15.0), alpha=1.0),
+}
+
+
+def workload(name: str, n: int | None = None):
+    """Components and conditions of a named workload (optionally the first
+    ``n`` mixtures of a fresh draw of size n with the same seed)."""
+    w = WORKLOADS[name]
+    comp = pseudo_components(w["nc"], w["comp_seed"])
+    cond = conditions(w["nc"], n if n is not None else w["n"], w["cond_seed"], w["T_range"], w["P_range"],
+                      w["alpha"])
+    return comp, cond
+
+
+# Paper Table 1 (Sec. 2.3): Pc [MPa], Tc [K], omega of the nine components;
+# the only nonzero BIP is CH4-CO2 = 0.0882.
+PAPER_TABLE1 = dict(
+    names=["CH4", "C2H6", "C3H8", "nC4H10", "nC5H12", "C6H14", "C7H16+", "CO2", "N2"],
+    Pc=[4.6, 4.875, 4.268, 3.796, 3.3332, 2.9688, 2.622, 7.382, 3.3944],
+    Tc=[190.55, 305.43, 369.82, 425.16, 467.15, 507.4, 604.5, 304.19, 126.25],
+    omega=[0.0111, 0.097, 0.1536, 0.2008, 0.2635, 0.296, 0.3565, 0.225, 0.039],
+)
+
+
+def paper_components(names) -> Components:
+    t = PAPER_TABLE1
+    idx = [t["names"].index(s) for s in names]
+    Tc = np.array([t["Tc"][i] for i in idx])
+    Pc = np.array([t["Pc"][i] for i in idx])
+    om = np.array([t["omega"][i] for i in idx])
+    k = np.zeros((len(idx), len(idx)))
+    if "CH4" in names and "CO2" in names:
+        a, b = names.index("CH4"), names.index("CO2")
+        k[a, b] = k[b, a] = 0.0882
+    return Components(Tc, Pc, om, k)
