@@ -1,0 +1,159 @@
+/*
+ * ptflash.h -- C ABI of the GB300 batched isothermal two-phase flash.
+ *
+ * Method: arXiv 2205.03090 ("PTFlash: a deep learning framework for
+ * isothermal two-phase equilibrium calculations").  SRK equation of state
+ * (Appendix A), Michelsen stability analysis with Wilson-initialised
+ * vapour-like and liquid-like trials (Sec. 2.2.1, Alg. 2), phase split by
+ * successive substitution on K with a Rachford-Rice solve (Sec. 2.2.2,
+ * Appendix C) and a trust-region Newton step on the Gibbs energy
+ * (Appendix B), run in the order of the flowchart of Sec. 2.2.3; the
+ * learned form adds the classifier / initializer networks of Sec. 4.
+ *
+ * Conventions shared by every call
+ *  - Arrays are structure-of-arrays with the mixture index fastest: the
+ *    composition of mixture m is z[i * n + m], i = 0 .. nc-1 (component-major).
+ *  - Pressures P and critical pressures Pc must use the same unit (the gas
+ *    constant cancels from the reduced EOS parameters); temperatures in K.
+ *  - Device entry points take DEVICE pointers owned by the caller and a CUDA
+ *    stream (cudaStream_t passed as void*, NULL = legacy default stream).
+ *    They enqueue work and return without synchronising; results are valid
+ *    once the stream has completed.  The context owns all scratch memory,
+ *    so calls that share one context must be ordered on one stream.
+ *  - Return value: 0 on success, a negative PTF_ERR_* code otherwise (no
+ *    call aborts the process).  ptflash_strerror() names a code.
+ *  - Per-mixture results carry a status bit set (PTF_ST_*).
+ *  - Single-phase output: nphase = 1, beta = 0, x = y = z, K = 1.
+ *    Two-phase output: nphase = 2, beta = vapour mole fraction theta_V in
+ *    (0,1), K_i = y_i / x_i, and y is always the lower-density phase
+ *    (larger compressibility factor).
+ */
+#ifndef PTFLASH_H
+#define PTFLASH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define PTF_OK 0
+#define PTF_ERR_INVALID_ARG (-1)   /* null pointer, bad size, bad component data */
+#define PTF_ERR_CUDA (-2)          /* a CUDA call failed (see ptflash_last_cuda_error) */
+#define PTF_ERR_NOT_READY (-3)     /* components (or network weights) not set */
+#define PTF_ERR_NO_MEMORY (-4)     /* device allocation failed */
+#define PTF_ERR_UNSUPPORTED (-5)   /* nc outside [2, 16] or beyond the context's nc_max */
+
+/* per-mixture status bits */
+#define PTF_ST_PRECHECK_UNSTABLE 1 /* the 3-iteration precheck proved instability (Sec. 2.2.3) */
+#define PTF_ST_STAB_RUN 2          /* stability analysis ran */
+#define PTF_ST_STAB_TR 4           /* a stability trial needed the trust region */
+#define PTF_ST_SPLIT_TR 8          /* the split needed the trust region */
+#define PTF_ST_MAXITER 16          /* an iteration cap was hit; result not converged */
+#define PTF_ST_COLLAPSE 32         /* split collapsed (trivial K / negative flash): single phase */
+#define PTF_ST_NONFINITE 64        /* non-finite input or state: single phase, values unusable */
+#define PTF_ST_NN_STABLE 128       /* learned form: classifier said stable (p >= p_r) */
+#define PTF_ST_NN_UNSTABLE 256     /* learned form: classifier said unstable (p <= p_l) */
+#define PTF_ST_NN_INIT 512         /* learned form: K initialised by the initializer network */
+
+typedef struct ptflash_ctx ptflash_ctx;
+
+/* Options of one flash call (NULL = defaults). */
+typedef struct {
+    int32_t use_nn;      /* 0 plain method (default); 1 classifier + initializer (Sec. 4.3) */
+    double p_l, p_r;     /* classifier thresholds (defaults 0.02, 0.98; Sec. 5.2) */
+    int32_t reserved[8];
+} ptflash_options;
+
+/*
+ * Create a context on the current CUDA device with device scratch for up to
+ * n_max mixtures of up to nc_max components per launch (larger batches are
+ * processed in chunks of n_max).  Allocates device memory (cudaMalloc).
+ * *out receives the context; release it with ptflash_destroy.
+ */
+int ptflash_create(ptflash_ctx** out, int nc_max, int64_t n_max);
+
+/* Free the context and its device memory (synchronises the device). */
+int ptflash_destroy(ptflash_ctx* ctx);
+
+/*
+ * Set the component system (Appendix A, Eq. mixing_rule and Table 1 data
+ * layout): HOST arrays Tc[nc] (K), Pc[nc] (pressure unit of P), omega[nc]
+ * (acentric factor), kij[nc*nc] (row-major binary interaction parameters,
+ * symmetric with zero diagonal).  2 <= nc <= nc_max <= 16.  Copies the data.
+ * PTF_ERR_INVALID_ARG for non-positive Tc/Pc, non-finite values, or an
+ * asymmetric / nonzero-diagonal kij.
+ */
+int ptflash_set_components(ptflash_ctx* ctx, int nc, const double* Tc, const double* Pc, const double* omega,
+                           const double* kij);
+
+/*
+ * Isothermal two-phase flash of n mixtures (Sec. 2.2.3; the learned form of
+ * Sec. 4.3 when opt->use_nn = 1).  DEVICE arrays: P[n], T[n], z[nc*n]
+ * inputs; nphase[n], beta[n], x[nc*n], y[nc*n], K[nc*n], status[n] outputs;
+ * iters[n] optional (NULL to skip): packed iteration counts
+ * split SS | split TR << 8 | stability SS << 16 | stability TR << 24
+ * (each field saturates at 255; the stability fields sum both trials).
+ * n == 0 is a no-op.  Outputs must not alias inputs.
+ */
+int ptflash_flash(ptflash_ctx* ctx, int64_t n, const double* P, const double* T, const double* z, int32_t* nphase,
+                  double* beta, double* x, double* y, double* K, int32_t* status, int32_t* iters,
+                  const ptflash_options* opt, void* stream);
+
+/*
+ * Same as ptflash_flash but every array is a HOST array (pinned memory gives
+ * the best copy rate).  Copies inputs to context-owned device buffers, runs
+ * the flash and copies the results back on `stream`, then synchronises the
+ * stream before returning.  The first host call allocates the context's
+ * staging buffers (n_max mixtures).
+ */
+int ptflash_flash_host(ptflash_ctx* ctx, int64_t n, const double* P, const double* T, const double* z,
+                       int32_t* nphase, double* beta, double* x, double* y, double* K, int32_t* status,
+                       int32_t* iters, const ptflash_options* opt, void* stream);
+
+/*
+ * Stability analysis alone (Sec. 2.2.1, Alg. 2: two Wilson trials, SS then
+ * trust region, stop at a stationary point or a negative tm).  DEVICE arrays:
+ * inputs P[n], T[n], z[nc*n]; outputs stable[n] (1 stable, 0 unstable:
+ * min tm < -1e-10), tm_min[n] (modified tangent-plane distance
+ * tm = 1 + sum W_i (ln W_i + ln phi_i(W) - ln z_i - ln phi_i(z) - 1) of the
+ * trial with the lower tm, at the point where it stopped), K[nc*n] (the K
+ * re-estimate z/W^L or W^V/z of Sec. 2.2.1), status[n].
+ */
+int ptflash_stability(ptflash_ctx* ctx, int64_t n, const double* P, const double* T, const double* z,
+                      int32_t* stable, double* tm_min, double* K, int32_t* status, void* stream);
+
+/*
+ * Queue sizes of the most recent ptflash_flash / ptflash_stability call on
+ * this context (synchronises the device): counts[0] mixtures sent to
+ * stability analysis, [1] mixtures sent to phase split, [2] stability trials
+ * that needed the trust region, [3] splits that needed the trust region,
+ * summed over chunks.  counts must hold 4 entries.
+ */
+int ptflash_last_counts(ptflash_ctx* ctx, int64_t* counts);
+
+/*
+ * Per-stage timing (the GPU counterpart of the paper's per-subroutine
+ * profiler, Table 4).  When enabled, each flash / stability call records a
+ * CUDA event before every stage kernel and waits for each chunk to finish
+ * (so profiled calls synchronise).  ptflash_last_stage_ms fills ms[0 .. count)
+ * with the milliseconds of the last call's stages, summed over chunks:
+ * [0] prep + precheck, [1] stability SS, [2] stability trust region,
+ * [3] stability decision, [4] split SS, [5] split trust region.
+ */
+int ptflash_set_profiling(ptflash_ctx* ctx, int enable);
+int ptflash_last_stage_ms(ptflash_ctx* ctx, double* ms, int count);
+
+/* Human-readable name of an error code. */
+const char* ptflash_strerror(int code);
+
+/* The last CUDA error string seen by this library (thread-local), or "". */
+const char* ptflash_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTFLASH_H */

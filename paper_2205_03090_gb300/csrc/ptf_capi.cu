@@ -1,0 +1,310 @@
+// ptf_capi.cu -- the C ABI declared in include/ptflash.h.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/ptflash.h"
+#include "ptf_launch.cuh"
+
+using namespace ptf;
+
+namespace {
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e) {
+    std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return PTF_ERR_CUDA;
+}
+#define PTF_CUDA(call)                              \
+    do {                                            \
+        cudaError_t _e = (call);                    \
+        if (_e != cudaSuccess) return cuda_fail(_e); \
+    } while (0)
+}  // namespace
+
+struct ptflash_ctx {
+    int device = 0;
+    int nc_max = 0;
+    int64_t n_max = 0;
+    int sm_count = 0;
+    CompHost comp{};
+    bool have_comp = false;
+    // device scratch
+    double* wsd = nullptr;    // (8 nc_max + 3) n_max doubles
+    int32_t* wsi = nullptr;   // 7 n_max + 64 int32
+    // staging for the host-pointer entry point
+    double* hd = nullptr;     // (4 nc_max + 3) n_max doubles: P, T, z, beta, x, y, K
+    int32_t* hi = nullptr;    // 3 n_max: nphase, status, iters
+    unsigned long long* acc = nullptr;  // device: queue sizes summed over the chunks of a call
+    bool profiling = false;
+    cudaEvent_t ev[kStages + 1] = {};
+    double stage_ms[kStages] = {};
+};
+
+// Fold the four queue counters of a chunk into the call's accumulator.
+__global__ void k_fold_counts(const int32_t* cnt, unsigned long long* acc) {
+    if (threadIdx.x < 4) acc[threadIdx.x] += (unsigned long long)cnt[threadIdx.x];
+}
+
+static WS make_ws(ptflash_ctx* c, int64_t n) {
+    const int nc = c->comp.nc;
+    WS w;
+    w.n = n;
+    double* p = c->wsd;
+    w.sA = p; p += (int64_t)nc * n;
+    w.B = p; p += (int64_t)nc * n;
+    w.lnz = p; p += (int64_t)nc * n;
+    w.d = p; p += (int64_t)nc * n;
+    w.lnK = p; p += (int64_t)nc * n;
+    w.nV = p; p += (int64_t)nc * n;
+    w.lnW = p; p += 2 * (int64_t)nc * n;
+    w.theta = p; p += n;
+    w.tm = p; p += 2 * n;
+    int32_t* q = c->wsi;
+    w.cnt = q; q += 64;
+    w.tflag = q; q += 2 * n;
+    w.q_stab = q; q += n;
+    w.q_split = q; q += n;
+    w.q_stab_tr = q; q += 2 * n;
+    w.q_split_tr = q; q += n;
+    return w;
+}
+
+static cudaError_t dispatch(ptflash_ctx* c, const WS& ws, const IO& io, int mode, cudaStream_t s) {
+    const int grid = c->sm_count * 8;
+    cudaEvent_t* ev = c->profiling ? c->ev : nullptr;
+    switch (c->comp.nc) {
+#define PTF_CASE(NC) \
+    case NC: return launch_plain<NC>(c->comp, ws, io, grid, mode, s, ev);
+        PTF_CASE(2) PTF_CASE(3) PTF_CASE(4) PTF_CASE(5) PTF_CASE(6) PTF_CASE(7) PTF_CASE(8) PTF_CASE(9)
+        PTF_CASE(10) PTF_CASE(11) PTF_CASE(12) PTF_CASE(13) PTF_CASE(14) PTF_CASE(15) PTF_CASE(16)
+#undef PTF_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+extern "C" {
+
+const char* ptflash_strerror(int code) {
+    switch (code) {
+        case PTF_OK: return "ok";
+        case PTF_ERR_INVALID_ARG: return "invalid argument";
+        case PTF_ERR_CUDA: return "CUDA error";
+        case PTF_ERR_NOT_READY: return "components not set";
+        case PTF_ERR_NO_MEMORY: return "device allocation failed";
+        case PTF_ERR_UNSUPPORTED: return "unsupported number of components";
+        default: return "unknown error";
+    }
+}
+
+const char* ptflash_last_cuda_error(void) { return g_cuda_err; }
+
+int ptflash_create(ptflash_ctx** out, int nc_max, int64_t n_max) {
+    if (!out) return PTF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nc_max < 2 || nc_max > 16) return PTF_ERR_UNSUPPORTED;
+    if (n_max < 1 || n_max > (int64_t)1 << 30) return PTF_ERR_INVALID_ARG;
+    ptflash_ctx* c = new (std::nothrow) ptflash_ctx();
+    if (!c) return PTF_ERR_NO_MEMORY;
+    c->nc_max = nc_max;
+    c->n_max = n_max;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e);
+    }
+    size_t nd = (size_t)(8 * nc_max + 3) * (size_t)n_max, ni = 7 * (size_t)n_max + 64;
+    if (cudaMalloc(&c->wsd, nd * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->wsi, ni * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&c->acc, 8 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->wsd);
+        cudaFree(c->wsi);
+        cudaFree(c->acc);
+        delete c;
+        return PTF_ERR_NO_MEMORY;
+    }
+    *out = c;
+    return PTF_OK;
+}
+
+int ptflash_destroy(ptflash_ctx* c) {
+    if (!c) return PTF_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    cudaFree(c->wsd);
+    cudaFree(c->wsi);
+    cudaFree(c->hd);
+    cudaFree(c->hi);
+    cudaFree(c->acc);
+    for (int k = 0; k <= kStages; k++)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    delete c;
+    return PTF_OK;
+}
+
+int ptflash_set_components(ptflash_ctx* c, int nc, const double* Tc, const double* Pc, const double* omega,
+                           const double* kij) {
+    if (!c || !Tc || !Pc || !omega || !kij) return PTF_ERR_INVALID_ARG;
+    if (nc < 2 || nc > 16 || nc > c->nc_max) return PTF_ERR_UNSUPPORTED;
+    for (int i = 0; i < nc; i++) {
+        if (!(Tc[i] > 0.0) || !(Pc[i] > 0.0) || !std::isfinite(Tc[i]) || !std::isfinite(Pc[i]) ||
+            !std::isfinite(omega[i]))
+            return PTF_ERR_INVALID_ARG;
+        for (int j = 0; j < nc; j++) {
+            double k = kij[i * nc + j];
+            if (!std::isfinite(k) || k != kij[j * nc + i] || (i == j && k != 0.0)) return PTF_ERR_INVALID_ARG;
+        }
+    }
+    CompHost h{};
+    h.nc = nc;
+    for (int i = 0; i < nc; i++) {
+        h.Tc[i] = Tc[i];
+        h.Pc[i] = Pc[i];
+        h.om[i] = omega[i];
+    }
+    for (int i = 0; i < nc * nc; i++) h.kij[i] = kij[i];
+    c->comp = h;
+    c->have_comp = true;
+    return PTF_OK;
+}
+
+static int run(ptflash_ctx* c, int64_t n, const double* P, const double* T, const double* z, int32_t* o_i,
+               double* o_d, double* x, double* y, double* K, int32_t* status, int32_t* iters, int mode,
+               bool zero_counts, cudaStream_t s) {
+    if (zero_counts) {
+        PTF_CUDA(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
+        for (int k = 0; k < kStages; k++) c->stage_ms[k] = 0.0;
+    }
+    for (int64_t m0 = 0; m0 < n; m0 += c->n_max) {
+        const int64_t cn = (n - m0 < c->n_max) ? n - m0 : c->n_max;
+        WS ws = make_ws(c, cn);
+        IO io;
+        io.ld = n;
+        io.P = P + m0;
+        io.T = T + m0;
+        io.z = z + m0;
+        io.nphase = o_i + m0;
+        io.beta = o_d + m0;
+        io.x = x ? x + m0 : nullptr;
+        io.y = y ? y + m0 : nullptr;
+        io.K = K + m0;
+        io.status = status + m0;
+        io.iters = iters ? iters + m0 : nullptr;
+        PTF_CUDA(cudaMemsetAsync(ws.cnt, 0, 64 * sizeof(int32_t), s));
+        PTF_CUDA(dispatch(c, ws, io, mode, s));
+        k_fold_counts<<<1, 32, 0, s>>>(ws.cnt, c->acc);
+        PTF_CUDA(cudaGetLastError());
+        if (c->profiling) {  // profiling mode waits for each chunk to read its stage times
+            PTF_CUDA(cudaEventSynchronize(c->ev[kStages]));
+            for (int k = 0; k < kStages; k++) {
+                float ms = 0.0f;
+                PTF_CUDA(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+                c->stage_ms[k] += ms;
+            }
+        }
+    }
+    return PTF_OK;
+}
+
+int ptflash_flash(ptflash_ctx* c, int64_t n, const double* P, const double* T, const double* z, int32_t* nphase,
+                  double* beta, double* x, double* y, double* K, int32_t* status, int32_t* iters,
+                  const ptflash_options* opt, void* stream) {
+    if (!c) return PTF_ERR_INVALID_ARG;
+    if (!c->have_comp) return PTF_ERR_NOT_READY;
+    if (n < 0) return PTF_ERR_INVALID_ARG;
+    if (n == 0) return PTF_OK;
+    if (!P || !T || !z || !nphase || !beta || !x || !y || !K || !status) return PTF_ERR_INVALID_ARG;
+    if (opt && opt->use_nn) return PTF_ERR_NOT_READY;
+    return run(c, n, P, T, z, nphase, beta, x, y, K, status, iters, 0, true, (cudaStream_t)stream);
+}
+
+int ptflash_stability(ptflash_ctx* c, int64_t n, const double* P, const double* T, const double* z,
+                      int32_t* stable, double* tm_min, double* K, int32_t* status, void* stream) {
+    if (!c) return PTF_ERR_INVALID_ARG;
+    if (!c->have_comp) return PTF_ERR_NOT_READY;
+    if (n < 0) return PTF_ERR_INVALID_ARG;
+    if (n == 0) return PTF_OK;
+    if (!P || !T || !z || !stable || !tm_min || !K || !status) return PTF_ERR_INVALID_ARG;
+    return run(c, n, P, T, z, stable, tm_min, nullptr, nullptr, K, status, nullptr, 1, true, (cudaStream_t)stream);
+}
+
+int ptflash_flash_host(ptflash_ctx* c, int64_t n, const double* P, const double* T, const double* z,
+                       int32_t* nphase, double* beta, double* x, double* y, double* K, int32_t* status,
+                       int32_t* iters, const ptflash_options* opt, void* stream) {
+    if (!c) return PTF_ERR_INVALID_ARG;
+    if (!c->have_comp) return PTF_ERR_NOT_READY;
+    if (n < 0) return PTF_ERR_INVALID_ARG;
+    if (n == 0) return PTF_OK;
+    if (!P || !T || !z || !nphase || !beta || !x || !y || !K || !status) return PTF_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nm = c->n_max;
+    const int nc = c->comp.nc;
+    if (!c->hd) {
+        if (cudaMalloc(&c->hd, (size_t)(4 * c->nc_max + 3) * nm * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&c->hi, (size_t)3 * nm * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(c->hd);
+            c->hd = nullptr;
+            return PTF_ERR_NO_MEMORY;
+        }
+    }
+    if (opt && opt->use_nn) return PTF_ERR_NOT_READY;
+    PTF_CUDA(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
+    for (int64_t m0 = 0; m0 < n; m0 += nm) {
+        const int64_t cn = (n - m0 < nm) ? n - m0 : nm;
+        double* dP = c->hd;
+        double* dT = dP + cn;
+        double* dz = dT + cn;
+        double* dbeta = dz + (int64_t)nc * cn;
+        double* dx = dbeta + cn;
+        double* dy = dx + (int64_t)nc * cn;
+        double* dK = dy + (int64_t)nc * cn;
+        int32_t* dnp = c->hi;
+        int32_t* dst = dnp + cn;
+        int32_t* dit = dst + cn;
+        const size_t rowb = (size_t)cn * sizeof(double), pitch = (size_t)n * sizeof(double);
+        PTF_CUDA(cudaMemcpyAsync(dP, P + m0, rowb, cudaMemcpyHostToDevice, s));
+        PTF_CUDA(cudaMemcpyAsync(dT, T + m0, rowb, cudaMemcpyHostToDevice, s));
+        PTF_CUDA(cudaMemcpy2DAsync(dz, rowb, z + m0, pitch, rowb, nc, cudaMemcpyHostToDevice, s));
+        int rc = run(c, cn, dP, dT, dz, dnp, dbeta, dx, dy, dK, dst, iters ? dit : nullptr, 0, false, s);
+        if (rc) return rc;
+        PTF_CUDA(cudaMemcpyAsync(nphase + m0, dnp, cn * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        PTF_CUDA(cudaMemcpyAsync(status + m0, dst, cn * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        if (iters) PTF_CUDA(cudaMemcpyAsync(iters + m0, dit, cn * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        PTF_CUDA(cudaMemcpyAsync(beta + m0, dbeta, rowb, cudaMemcpyDeviceToHost, s));
+        PTF_CUDA(cudaMemcpy2DAsync(x + m0, pitch, dx, rowb, rowb, nc, cudaMemcpyDeviceToHost, s));
+        PTF_CUDA(cudaMemcpy2DAsync(y + m0, pitch, dy, rowb, rowb, nc, cudaMemcpyDeviceToHost, s));
+        PTF_CUDA(cudaMemcpy2DAsync(K + m0, pitch, dK, rowb, rowb, nc, cudaMemcpyDeviceToHost, s));
+        PTF_CUDA(cudaStreamSynchronize(s));
+    }
+    return PTF_OK;
+}
+
+int ptflash_set_profiling(ptflash_ctx* c, int enable) {
+    if (!c) return PTF_ERR_INVALID_ARG;
+    if (enable && !c->ev[0]) {
+        for (int k = 0; k <= kStages; k++) PTF_CUDA(cudaEventCreate(&c->ev[k]));
+    }
+    c->profiling = enable != 0;
+    return PTF_OK;
+}
+
+int ptflash_last_stage_ms(ptflash_ctx* c, double* ms, int count) {
+    if (!c || !ms || count < 0) return PTF_ERR_INVALID_ARG;
+    for (int k = 0; k < count && k < kStages; k++) ms[k] = c->stage_ms[k];
+    return PTF_OK;
+}
+
+int ptflash_last_counts(ptflash_ctx* c, int64_t* counts) {
+    if (!c || !counts) return PTF_ERR_INVALID_ARG;
+    unsigned long long a[4];
+    PTF_CUDA(cudaDeviceSynchronize());
+    PTF_CUDA(cudaMemcpy(a, c->acc, sizeof(a), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 4; k++) counts[k] = (int64_t)a[k];
+    return PTF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,469 @@
+// ptf_device.cuh -- per-thread FP64 building blocks of the flash (sm_103a).
+//
+// One mixture per thread; NC (number of components) is a template parameter
+// so per-component vectors live in registers.  Everything here is FP64
+// except the FP32 starting guess of the cubic root, which FP64 Halley
+// iterations then refine to full precision.
+//
+// Paper references (arXiv 2205.03090): SRK EOS and mixing rules (Appendix A,
+// Eqs. mixing_rule, cubic_Z, halley, lnphi), Wilson K (Eq. wilson),
+// Rachford-Rice (Eq. RR, Appendix C, Eq. RR_helper), trust-region method
+// (Appendix B, Eqs. tr_sa, analysis_grad/hess, newton_splitter,
+// split_grad/hess), DEM (Sec. 2.2.1).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ptf {
+
+// ---------------------------------------------------------------------------
+// Constants printed in the paper and the method's controls
+// ---------------------------------------------------------------------------
+constexpr double kOmegaA = 0.42748;   // Eq. a_i
+constexpr double kOmegaB = 0.08664;   // Eq. b_i
+constexpr double kWilson = 5.373;     // Eq. wilson
+constexpr double kTolStab = 1e-6;     // Sec. 2.2.1, Appendix B.1
+constexpr double kTolSplitTR = 1e-8;  // Appendix B.2
+constexpr double kTolFug = 1e-10;     // fugacity residual of a converged split
+constexpr int kSSStab = 9;            // Alg. 2
+constexpr int kTRStab = 20;           // Alg. 2
+constexpr int kSSSplit = 9;           // Sec. 2.2.2
+constexpr int kTRSplit = 20;          // same cap as the stability TR
+constexpr int kNewtonPolish = 5;      // Newton steps after a split TR run
+constexpr int kPrecheck = 3;          // Sec. 2.2.3
+constexpr double kEpsNeg = 1e-10;     // "negative" tm / tpd / Delta G
+constexpr double kTrivialLnK = 1e-6;  // split collapsed to K = 1
+constexpr double kPredTrust = 1e-12;  // ratio test trusted above this
+
+// status bits (same values as documented in include/ptflash.h)
+constexpr int ST_PRECHECK_UNSTABLE = 1;
+constexpr int ST_STAB_RUN = 2;
+constexpr int ST_STAB_TR = 4;
+constexpr int ST_SPLIT_TR = 8;
+constexpr int ST_MAXITER = 16;
+constexpr int ST_COLLAPSE = 32;
+constexpr int ST_NONFINITE = 64;
+constexpr int ST_NN_STABLE = 128;
+constexpr int ST_NN_UNSTABLE = 256;
+constexpr int ST_NN_INIT = 512;
+
+// Component table, passed by value as a kernel parameter (constant bank:
+// every access is a uniform broadcast).
+template <int NC>
+struct Comp {
+    double kk[NC * NC];  // 1 - k_ij
+    double Tc[NC], Pc[NC], lnPc[NC], mi[NC], wc[NC];  // wc = 5.373 (1 + omega)
+};
+
+// Per-mixture EOS constants: sqrt(A_i) and B_i (reduced, R cancels).
+template <int NC>
+struct Mix {
+    double sA[NC], B[NC];
+};
+
+// Appendix A: A_i = 0.42748 alpha_i (P/Pc)(Tc/T)^2, B_i = 0.08664 (P/Pc)(Tc/T),
+// alpha_i = [1 + m_i (1 - sqrt(T/Tc))]^2.
+template <int NC>
+__device__ __forceinline__ void mix_init(const Comp<NC>& cp, double P, double T, Mix<NC>& mx) {
+    double invT = 1.0 / T;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        double tr = T / cp.Tc[i];
+        double a = 1.0 + cp.mi[i] * (1.0 - sqrt(tr));
+        double pr = P / cp.Pc[i];
+        double trinv = cp.Tc[i] * invT;
+        // sqrt(A_i) = sqrt(0.42748 pr) |a| trinv
+        mx.sA[i] = sqrt(kOmegaA * pr) * fabs(a) * trinv;
+        mx.B[i] = kOmegaB * pr * trinv;
+    }
+}
+
+// Eq. wilson
+template <int NC>
+__device__ __forceinline__ void wilson(const Comp<NC>& cp, double P, double T, double* lnK) {
+    double lnP = log(P), invT = 1.0 / T;
+#pragma unroll
+    for (int i = 0; i < NC; i++) lnK[i] = cp.lnPc[i] - lnP + cp.wc[i] * (1.0 - cp.Tc[i] * invT);
+}
+
+// ---------------------------------------------------------------------------
+// Cubic (Eq. cubic_Z) f(Z) = Z^3 - Z^2 + r1 Z - r0, r1 = A - B - B^2, r0 = AB.
+// f(B) = -2B^2 < 0 and f(1+B) = A > 0, so (B, 1+B] holds a sign change and
+// every admissible root (Z > B) lies in it.  The number of real roots follows
+// from the values of f at its critical points.  One root is found by Halley
+// iterations (Eq. halley) kept inside the sign-change bracket (bisection when
+// a step leaves it, so the iteration cannot stall at an extremum): an FP32
+// run seeds the FP64 run, which stops once a Halley step is below 1e-8
+// relative (Appendix A).  With three real roots, deflation (Appendix A) gives
+// the other two, each polished by one FP64 Newton step on the original cubic.
+// Among admissible roots the smallest and the largest are compared by the
+// residual Gibbs energy gbar(Z) = Z - 1 - ln(Z - B) - (A/B) ln(1 + B/Z).
+// ---------------------------------------------------------------------------
+struct Root {
+    double Z, lzb, L;  // chosen root, ln(Z - B), ln(1 + B/Z)
+};
+
+__device__ __forceinline__ double cub_f(double Z, double r1, double r0) { return fma(fma(Z - 1.0, Z, r1), Z, -r0); }
+__device__ __forceinline__ double cub_df(double Z, double r1) { return fma(fma(3.0, Z, -2.0), Z, r1); }
+
+__device__ __forceinline__ Root cubic_select(double A, double B) {
+    const double r1 = A - B * (1.0 + B), r0 = A * B;
+    // real-root count from the critical points of f (local max zm, local min zp)
+    bool three = false;
+    const double dcrit = 4.0 - 12.0 * r1;
+    if (dcrit > 0.0) {
+        const double sq = sqrt(dcrit);
+        const double fm = cub_f((2.0 - sq) * (1.0 / 6.0), r1, r0), fpv = cub_f((2.0 + sq) * (1.0 / 6.0), r1, r0);
+        three = !(fm < 0.0) && !(fpv > 0.0);
+    }
+    // FP32 seed: bracketed Halley on (B, 1 + B]
+    float lof = (float)B, hif = 1.0f + (float)B, zf = hif;
+    {
+        const float r1f = (float)r1, r0f = (float)r0;
+#pragma unroll 1
+        for (int it = 0; it < 40; it++) {
+            float f = fmaf(fmaf(zf - 1.0f, zf, r1f), zf, -r0f);
+            if (f < 0.0f) lof = zf; else hif = zf;
+            float fp = fmaf(fmaf(3.0f, zf, -2.0f), zf, r1f);
+            float fpp = fmaf(6.0f, zf, -2.0f);
+            float zn = zf - 2.0f * f * fp / (2.0f * fp * fp - f * fpp);
+            if (!(zn > lof && zn < hif)) zn = 0.5f * (lof + hif);
+            bool done = fabsf(zn - zf) <= 1e-6f * zf;
+            zf = zn;
+            if (done) break;
+        }
+    }
+    // FP64 bracketed Halley from the seed
+    double lo = B, hi = 1.0 + B, z0 = (double)zf;
+    if (!(z0 > lo && z0 < hi)) z0 = 0.5 * (lo + hi);
+#pragma unroll 1
+    for (int it = 0; it < 100; it++) {
+        double f = cub_f(z0, r1, r0);
+        if (f < 0.0) lo = z0; else if (f > 0.0) hi = z0; else break;
+        double fp = cub_df(z0, r1);
+        double fpp = fma(6.0, z0, -2.0);
+        double zn = z0 - 2.0 * f * fp / (2.0 * fp * fp - f * fpp);
+        if (!(zn > lo && zn < hi)) {
+            z0 = 0.5 * (lo + hi);  // bisection
+            if (hi - lo <= 1e-15 * z0) break;
+            continue;
+        }
+        bool done = fabs(zn - z0) <= 1e-8 * fabs(zn);
+        z0 = zn;
+        if (done) break;
+    }
+    double zl = z0, zv = z0;
+    if (three) {
+        // deflation: f = (Z - z0)(Z^2 + p Z + q), p = z0 - 1, q = p z0 + r1
+        const double p = z0 - 1.0, q = fma(p, z0, r1);
+        const double sd = sqrt(fmax(p * p - 4.0 * q, 0.0));
+        const double t = -0.5 * (p + copysign(sd, p));  // stable quadratic roots
+        const double q1 = t, q2 = (t != 0.0) ? q / t : t;
+        zl = fmin(z0, fmin(q1, q2));
+        zv = fmax(z0, fmax(q1, q2));
+        const double dl = cub_df(zl, r1), dv = cub_df(zv, r1);
+        if (dl != 0.0) zl -= cub_f(zl, r1, r0) / dl;
+        if (dv != 0.0) zv -= cub_f(zv, r1, r0) / dv;
+    }
+    Root r;
+    const double lzbv = log(zv - B), Lv = log(1.0 + B / zv);
+    r.Z = zv;
+    r.lzb = lzbv;
+    r.L = Lv;
+    if (zl > B && zl < zv) {
+        const double lzbl = log(zl - B), Ll = log(1.0 + B / zl);
+        const double AB = A / B;
+        const double gl = zl - lzbl - AB * Ll, gv = zv - lzbv - AB * Lv;
+        if (gl < gv) {
+            r.Z = zl;
+            r.lzb = lzbl;
+            r.L = Ll;
+        }
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Phase evaluation: mixing rules (Eq. mixing_rule), root, ln phi (Eq. lnphi):
+// ln phi_i = B_i [(Z - 1)/B + A L / B^2] - ln(Z - B) - psi_i (2 L / B),
+// psi_i = sqrt(A_i) sum_j (1 - k_ij) sqrt(A_j) c_j.
+// ---------------------------------------------------------------------------
+template <int NC>
+struct Phase {
+    double A, B, Z, L;
+    double psi[NC];
+    double lnphi[NC];
+};
+
+template <int NC>
+__device__ __forceinline__ void eos(const Comp<NC>& cp, const Mix<NC>& mx, const double* c, Phase<NC>& ph) {
+    double sc[NC];
+#pragma unroll
+    for (int j = 0; j < NC; j++) sc[j] = mx.sA[j] * c[j];
+    double A = 0.0, B = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        double acc = sc[i];  // k_ii = 0
+#pragma unroll
+        for (int j = 0; j < NC; j++)
+            if (j != i) acc = fma(cp.kk[i * NC + j], sc[j], acc);
+        ph.psi[i] = mx.sA[i] * acc;
+        A = fma(c[i], ph.psi[i], A);
+        B = fma(c[i], mx.B[i], B);
+    }
+    Root r = cubic_select(A, B);
+    double invB = 1.0 / B;
+    double u = ((r.Z - 1.0) + A * r.L * invB) * invB;
+    double v = 2.0 * r.L * invB;
+#pragma unroll
+    for (int i = 0; i < NC; i++) ph.lnphi[i] = fma(mx.B[i], u, -r.lzb) - ph.psi[i] * v;
+    ph.A = A;
+    ph.B = B;
+    ph.Z = r.Z;
+    ph.L = r.L;
+}
+
+// ---------------------------------------------------------------------------
+// J_ij = n_T d ln phi_i / d n_j (Appendix A, last paragraph), lower triangle
+// of the symmetric matrix, packed row-wise: J[i (i+1)/2 + j], j <= i.
+// Differentiating Eq. lnphi through A(c), B(c), psi(c) and the implicit Z of
+// the cubic with c_k independent gives f_ik; J_ij = f_ij - sum_k c_k f_ik,
+// where the row sums reduce to closed forms (e_i is homogeneous of degree 0).
+// ---------------------------------------------------------------------------
+template <int NC>
+__device__ __forceinline__ void dlnphi_dn(const Comp<NC>& cp, const Mix<NC>& mx, const double* c, const Phase<NC>& ph,
+                                          double* J) {
+    const double A = ph.A, B = ph.B, Z = ph.Z, L = ph.L;
+    const double invB = 1.0 / B, invZB = 1.0 / (Z - B), invZpB = 1.0 / (Z + B), invZ = 1.0 / Z;
+    const double FZ = fma(fma(3.0, Z, -2.0), Z, A - B - B * B);
+    const double FA = Z - B, FB = -Z - 2.0 * B * Z - A;
+    const double invFZ = 1.0 / FZ;
+    double Zk[NC], Lk[NC], e[NC], bb[NC];
+    // Zc = sum c_k Z_k, Lc = sum c_k L_k
+    const double Zc = -(FA * 2.0 * A + FB * B) * invFZ;
+    const double Lc = (Zc + B) * invZpB - Zc * invZ;
+#pragma unroll
+    for (int k = 0; k < NC; k++) {
+        Zk[k] = -(FA * 2.0 * ph.psi[k] + FB * mx.B[k]) * invFZ;
+        Lk[k] = (Zk[k] + mx.B[k]) * invZpB - Zk[k] * invZ;
+        bb[k] = mx.B[k] * invB;
+        e[k] = (A * bb[k] - 2.0 * ph.psi[k]) * invB;
+    }
+    const double Zm1 = Z - 1.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        // row constant: -(sum_k c_k f_ik) + terms independent of j
+        const double si = -bb[i] * Zm1 + bb[i] * Zc - (Zc - B) * invZB + e[i] * Lc;
+#pragma unroll
+        for (int j = 0; j <= i; j++) {
+            double aij = (i == j) ? mx.sA[i] * mx.sA[i] : cp.kk[i * NC + j] * mx.sA[i] * mx.sA[j];
+            double de = 2.0 * invB * (ph.psi[j] * bb[i] - A * bb[i] * bb[j] - aij + ph.psi[i] * bb[j]);
+            double f = -bb[i] * bb[j] * Zm1 + bb[i] * Zk[j] - (Zk[j] - mx.B[j]) * invZB + de * L + e[i] * Lk[j];
+            J[i * (i + 1) / 2 + j] = f - si;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Rachford-Rice (Eq. RR) on the Leibovici-Neoschil window (Appendix C):
+// Newton on h = (theta - a_l)(a_r - theta) f_RR inside a shrinking bracket,
+// bisection when Newton leaves it; run to full precision.  Returns false if
+// K does not bracket 1.  On success t[i] = 1 / (1 + (K_i - 1) theta).
+// ---------------------------------------------------------------------------
+template <int NC>
+__device__ __forceinline__ bool rachford_rice(const double* z, const double* K, double& theta, double* t) {
+    double kmax = K[0], kmin = K[0];
+#pragma unroll
+    for (int i = 1; i < NC; i++) {
+        kmax = fmax(kmax, K[i]);
+        kmin = fmin(kmin, K[i]);
+    }
+    if (!(kmax > 1.0 && kmin < 1.0)) return false;
+    const double al = 1.0 / (1.0 - kmax), ar = 1.0 / (1.0 - kmin);
+    double lo = al, hi = ar;
+    double th = theta;
+    if (!(th > lo && th < hi)) th = 0.5 * (fmax(lo, 0.0) + fmin(hi, 1.0));
+    double km1[NC];
+#pragma unroll
+    for (int i = 0; i < NC; i++) km1[i] = K[i] - 1.0;
+#pragma unroll 1
+    for (int it = 0; it < 200; it++) {
+        double f = 0.0, fp = 0.0;
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            double ti = 1.0 / fma(km1[i], th, 1.0);
+            double a = km1[i] * ti;
+            f = fma(a, z[i], f);
+            fp = fma(-a * a, z[i], fp);
+        }
+        if (f > 0.0) lo = th; else hi = th;
+        double g1 = th - al, g2 = ar - th;
+        double h = g1 * g2 * f;
+        double hp = (g2 - g1) * f + g1 * g2 * fp;
+        double tn = th - h / hp;
+        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+        double step = fabs(tn - th);
+        th = tn;
+        if (step <= 1e-15 * fmax(1.0, fabs(th)) || lo >= hi) break;
+    }
+#pragma unroll
+    for (int i = 0; i < NC; i++) t[i] = 1.0 / fma(km1[i], th, 1.0);
+    theta = th;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Small dense linear algebra on packed lower triangles (n <= 16), per thread.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// Cholesky of (H + eta diag(1)) in the scaled space; returns false if not PD.
+template <int NC>
+__device__ __forceinline__ bool cholesky(const double* H, double eta, double* Lf) {
+#pragma unroll 1
+    for (int j = 0; j < NC; j++) {
+        double d = H[tri(j, j)] + eta;
+#pragma unroll 1
+        for (int k = 0; k < j; k++) d = fma(-Lf[tri(j, k)], Lf[tri(j, k)], d);
+        if (!(d > 0.0)) return false;
+        double ljj = sqrt(d), inv = 1.0 / ljj;
+        Lf[tri(j, j)] = ljj;
+#pragma unroll 1
+        for (int i = j + 1; i < NC; i++) {
+            double s = H[tri(i, j)];
+#pragma unroll 1
+            for (int k = 0; k < j; k++) s = fma(-Lf[tri(i, k)], Lf[tri(j, k)], s);
+            Lf[tri(i, j)] = s * inv;
+        }
+    }
+    return true;
+}
+
+// Solve L y = b (forward) in place
+template <int NC>
+__device__ __forceinline__ void fwd(const double* Lf, double* b) {
+#pragma unroll 1
+    for (int i = 0; i < NC; i++) {
+        double s = b[i];
+#pragma unroll 1
+        for (int k = 0; k < i; k++) s = fma(-Lf[tri(i, k)], b[k], s);
+        b[i] = s / Lf[tri(i, i)];
+    }
+}
+
+// Solve L^T x = b (backward) in place
+template <int NC>
+__device__ __forceinline__ void bwd(const double* Lf, double* b) {
+#pragma unroll 1
+    for (int i = NC - 1; i >= 0; i--) {
+        double s = b[i];
+#pragma unroll 1
+        for (int k = i + 1; k < NC; k++) s = fma(-Lf[tri(k, i)], b[k], s);
+        b[i] = s / Lf[tri(i, i)];
+    }
+}
+
+// Newton step d = -H^{-1} g in the scaled space (H already scaled).  Returns
+// false if H is not positive definite.
+template <int NC>
+__device__ __forceinline__ bool newton_scaled(const double* Hs, const double* gs, double* Lf, double* d) {
+    if (!cholesky<NC>(Hs, 0.0, Lf)) return false;
+    for (int i = 0; i < NC; i++) d[i] = -gs[i];
+    fwd<NC>(Lf, d);
+    bwd<NC>(Lf, d);
+    return true;
+}
+
+// Trust-region subproblem (Appendix B) in the scaled space: minimise
+// gs.u + u.Hs.u/2 subject to ||u|| <= radius.  Hebden / More-Sorensen Newton
+// iteration on 1/||u(eta)|| - 1/radius with Cholesky factorisations,
+// safeguarded by a bracket [elo, ehi]; solved to 1e-10 relative on ||u||.
+template <int NC>
+__device__ __forceinline__ void tr_step_scaled(const double* Hs, const double* gs, double radius, double* Lf, double* u) {
+    double gn = 0.0, hn1 = 0.0, mind = 1e300;
+    for (int i = 0; i < NC; i++) {
+        gn = fma(gs[i], gs[i], gn);
+        double rs = 0.0;
+        for (int j = 0; j < NC; j++) rs += fabs(Hs[i >= j ? tri(i, j) : tri(j, i)]);
+        hn1 = fmax(hn1, rs);
+        mind = fmin(mind, Hs[tri(i, i)]);
+    }
+    gn = sqrt(gn);
+    double elo = fmax(0.0, fmax(-mind, gn / radius - hn1));
+    double ehi = gn / radius + hn1;
+    // eta = 0 first: the Newton step when it fits
+    double eta = 0.0;
+    if (cholesky<NC>(Hs, 0.0, Lf)) {
+        for (int i = 0; i < NC; i++) u[i] = -gs[i];
+        fwd<NC>(Lf, u);
+        bwd<NC>(Lf, u);
+        double un = 0.0;
+        for (int i = 0; i < NC; i++) un = fma(u[i], u[i], un);
+        if (sqrt(un) <= radius) return;
+        elo = fmax(elo, 0.0);
+        eta = fmax(elo, 1e-300);
+    } else {
+        eta = fmax(elo, 1e-12 * fmax(1.0, hn1));
+    }
+#pragma unroll 1
+    for (int it = 0; it < 100; it++) {
+        if (!cholesky<NC>(Hs, eta, Lf)) {
+            elo = eta;
+            eta = fmax(0.5 * (elo + ehi), 1.0001 * elo + 1e-300);
+            continue;
+        }
+        for (int i = 0; i < NC; i++) u[i] = -gs[i];
+        fwd<NC>(Lf, u);
+        bwd<NC>(Lf, u);
+        double un = 0.0;
+        for (int i = 0; i < NC; i++) un = fma(u[i], u[i], un);
+        un = sqrt(un);
+        if (fabs(un - radius) <= 1e-10 * radius) return;
+        if (un < radius) ehi = eta; else elo = eta;
+        // q = L^{-1} u ; Newton update of the secular equation
+        double q[NC];
+        for (int i = 0; i < NC; i++) q[i] = u[i];
+        fwd<NC>(Lf, q);
+        double qn = 0.0;
+        for (int i = 0; i < NC; i++) qn = fma(q[i], q[i], qn);
+        double en = eta + (un * un / qn) * (un - radius) / radius;
+        if (!(en > elo && en < ehi)) en = 0.5 * (elo + ehi);
+        if (en == eta) return;
+        eta = en;
+    }
+}
+
+// DEM factor (Sec. 2.2.1): lambda = (dk.d1)/(d1.d1) once settled (previous
+// estimate within 10 %), updates shrinking and nearly parallel (cos^2 >= 0.99)
+// and 0 < lambda < 1; returns lambda / (1 - lambda) or 0.
+template <int NC>
+__device__ __forceinline__ double dem_factor(const double* dk, const double* d1, const double* d2) {
+    double n0 = 0.0, n1 = 0.0, n2 = 0.0, p01 = 0.0, p12 = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        n0 = fma(dk[i], dk[i], n0);
+        n1 = fma(d1[i], d1[i], n1);
+        n2 = fma(d2[i], d2[i], n2);
+        p01 = fma(dk[i], d1[i], p01);
+        p12 = fma(d1[i], d2[i], p12);
+    }
+    if (!(n1 > 0.0 && n2 > 0.0) || !(n0 < n1)) return 0.0;
+    double lam = p01 / n1, lam1 = p12 / n2;
+    if (!(lam > 0.0 && lam < 1.0)) return 0.0;
+    if (!(fabs(lam - lam1) <= 0.1 * lam)) return 0.0;
+    if (!(p01 * p01 >= 0.99 * n0 * n1)) return 0.0;
+    return lam / (1.0 - lam);
+}
+
+template <int NC>
+__device__ __forceinline__ double maxabs(const double* v) {
+    double r = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) r = fmax(r, fabs(v[i]));
+#pragma unroll
+    for (int i = 0; i < NC; i++)
+        if (v[i] != v[i]) r = INFINITY;
+    return r;
+}
+
+}  // namespace ptf

@@ -1,0 +1,828 @@
+// ptf_kernels.cuh -- stage kernels of the plain flash (Sec. 2.2.3 flowchart).
+//
+// Stages communicate through device-resident index queues (the GPU form of
+// the paper's synchronizer and barriers, Sec. 3 and Alg. 1): every kernel
+// reads its queue length from device memory, so a whole flash is a fixed
+// sequence of launches on one stream with no host synchronisation.
+//
+//   prep_precheck : per-mixture constants, ln z, d = ln z + ln phi(z), Wilson
+//                   K, 3 split-SS iterations, tpd tests -> STAB or SPLIT queue
+//   stab_ss       : one item per (mixture, trial); SS with DEM (Eq.
+//                   ss_analyser) -> done or STAB_TR queue
+//   stab_tr       : trust region in beta = 2 sqrt(W) (Appendix B.1)
+//   stab_decide   : label, K re-estimate (Sec. 2.2.1) -> SPLIT queue or done
+//   split_ss      : SS with DEM and Rachford-Rice (Sec. 2.2.2) -> done or
+//                   SPLIT_TR queue
+//   split_tr      : trust region on G in n^V (Appendix B.2) + Newton polish
+//
+// All arrays are SoA with the mixture index fastest ([i * n + m]), so a warp
+// of consecutive mixtures reads and writes coalesced 256-byte rows.
+#pragma once
+#include "ptf_device.cuh"
+
+namespace ptf {
+
+struct WS {
+    int64_t n;  // mixtures in this chunk (stride of every SoA array)
+    double *sA, *B, *lnz, *d, *lnK, *theta, *nV;  // [NC n] (theta: [n])
+    double* lnW;       // [2 NC n]: trial t, component i at ((t NC + i) n + m)
+    double* tm;        // [2 n]
+    int32_t* tflag;    // [2 n]: ss iters | tr iters << 8 | used_tr << 16 | maxiter << 17 | nonfinite << 18
+    int32_t *q_stab, *q_split, *q_stab_tr, *q_split_tr;
+    int32_t* cnt;      // [0] stab, [1] split, [2] stab_tr (items), [3] split_tr
+};
+
+struct IO {
+    int64_t ld;  // leading dimension (stride between components) of z, x, y, K
+    const double *P, *T, *z;
+    int32_t* nphase;
+    double *beta, *x, *y, *K;
+    int32_t* status;
+    int32_t* iters;  // packed: split SS | split TR << 8 | stab SS << 16 | stab TR << 24 (may be null)
+};
+
+enum { Q_STAB = 0, Q_SPLIT = 1, Q_STAB_TR = 2, Q_SPLIT_TR = 3 };
+
+// Warp-aggregated append: every lane of the warp must call it (full mask).
+__device__ __forceinline__ void warp_append(int32_t* cnt, int32_t* queue, bool pred, int32_t value) {
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (pred) queue[base + __popc(m & ((1u << lane) - 1u))] = value;
+}
+
+// Loop over items in whole-warp rounds so that queue appends see a converged
+// warp: item = round_base + lane, valid = item < len.
+#define PTF_WARP_ROUNDS(len, item, valid)                                                              \
+    for (int64_t _rb = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)); _rb < (len);          \
+         _rb += (int64_t)gridDim.x * blockDim.x)                                                       \
+        for (int64_t item = _rb + (threadIdx.x & 31), _once = 1; _once; _once = 0)                     \
+            for (bool valid = item < (len); _once; _once = 0)
+
+template <int NC>
+__device__ __forceinline__ void load_mix(const WS& ws, int64_t m, Mix<NC>& mx) {
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        mx.sA[i] = ws.sA[i * ws.n + m];
+        mx.B[i] = ws.B[i * ws.n + m];
+    }
+}
+
+template <int NC>
+__device__ __forceinline__ void write_single(const IO& io, int64_t m, const double* z) {
+    const int64_t n = io.ld;
+    io.nphase[m] = 1;
+    io.beta[m] = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        io.x[i * n + m] = z[i];
+        io.y[i * n + m] = z[i];
+        io.K[i * n + m] = 1.0;
+    }
+}
+
+// Two-phase result with canonical labels: y is the lower-density phase.
+template <int NC>
+__device__ __forceinline__ void write_two(const IO& io, int64_t m, double th, const double* x, const double* y,
+                                          double ZL, double ZV) {
+    const int64_t n = io.ld;
+    const bool swap = ZV < ZL;
+    io.nphase[m] = 2;
+    io.beta[m] = swap ? 1.0 - th : th;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        double xi = swap ? y[i] : x[i], yi = swap ? x[i] : y[i];
+        io.x[i * n + m] = xi;
+        io.y[i * n + m] = yi;
+        io.K[i * n + m] = yi / xi;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// prep + precheck (Sec. 2.2.3): three SS iterations from Wilson K.
+// ---------------------------------------------------------------------------
+// Returns the route of mixture m: 0 done, 1 stability queue, 2 split queue.
+template <int NC, bool PRECHECK>
+__device__ __forceinline__ int prep_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t m) {
+    const int64_t n = ws.n;
+    bool to_stab = false, to_split = false;
+    {
+        {
+            const double P = io.P[m], T = io.T[m];
+            double z[NC], lnz[NC], d[NC];
+#pragma unroll
+            for (int i = 0; i < NC; i++) z[i] = io.z[i * io.ld + m];
+            Mix<NC> mx;
+            mix_init<NC>(cp, P, T, mx);
+            Phase<NC> pz;
+            eos<NC>(cp, mx, z, pz);
+            bool finite = true;
+#pragma unroll
+            for (int i = 0; i < NC; i++) {
+                lnz[i] = log(z[i]);
+                d[i] = lnz[i] + pz.lnphi[i];
+                finite = finite && isfinite(d[i]);
+                ws.sA[i * n + m] = mx.sA[i];
+                ws.B[i * n + m] = mx.B[i];
+                ws.lnz[i * n + m] = lnz[i];
+                ws.d[i * n + m] = d[i];
+            }
+            int32_t st = 0;
+            if (!finite || !(P > 0.0 && T > 0.0)) {
+                st = ST_NONFINITE;
+                if (PRECHECK) {
+                    write_single<NC>(io, m, z);
+                } else {  // stability-only outputs: stable, tm = NaN, K = 1
+                    io.nphase[m] = 1;
+                    io.beta[m] = NAN;
+#pragma unroll
+                    for (int i = 0; i < NC; i++) io.K[i * io.ld + m] = 1.0;
+                }
+            } else if (!PRECHECK) {
+                to_stab = true;
+                st = ST_STAB_RUN;
+            } else {
+                double lnK[NC], K[NC], t[NC], x[NC], y[NC];
+                wilson<NC>(cp, P, T, lnK);
+                Phase<NC> pl, pv;
+                double th = 0.5;
+                bool stab = false;
+#pragma unroll 1
+                for (int it = 0; it < kPrecheck; it++) {
+#pragma unroll
+                    for (int i = 0; i < NC; i++) K[i] = exp(lnK[i]);
+                    if (!rachford_rice<NC>(z, K, th, t) || !(th > 0.0 && th < 1.0)) {
+                        stab = true;
+                        break;
+                    }
+#pragma unroll
+                    for (int i = 0; i < NC; i++) {
+                        x[i] = z[i] * t[i];
+                        y[i] = K[i] * x[i];
+                    }
+                    eos<NC>(cp, mx, x, pl);
+                    eos<NC>(cp, mx, y, pv);
+#pragma unroll
+                    for (int i = 0; i < NC; i++) lnK[i] -= lnK[i] + pv.lnphi[i] - pl.lnphi[i];
+                }
+                if (!stab) {
+                    // Eq. tpd for the current phases; Delta G = (1-theta) tpd(x) + theta tpd(y)
+                    double tx = 0.0, ty = 0.0;
+#pragma unroll
+                    for (int i = 0; i < NC; i++) {
+                        double lx = log(x[i]);
+                        double ly = log(y[i]);
+                        tx = fma(x[i], lx + pl.lnphi[i] - d[i], tx);
+                        ty = fma(y[i], ly + pv.lnphi[i] - d[i], ty);
+                    }
+                    double dG = (1.0 - th) * tx + th * ty;
+                    stab = !(tx < -kEpsNeg || ty < -kEpsNeg || dG < -kEpsNeg);
+                }
+                if (stab) {
+                    to_stab = true;
+                    st = ST_STAB_RUN;
+                } else {
+                    to_split = true;
+                    st = ST_PRECHECK_UNSTABLE;
+#pragma unroll
+                    for (int i = 0; i < NC; i++) ws.lnK[i * n + m] = lnK[i];
+                }
+            }
+            io.status[m] = st;
+            if (io.iters) io.iters[m] = 0;
+        }
+    }
+    return to_stab ? 1 : (to_split ? 2 : 0);
+}
+
+template <int NC, bool PRECHECK>
+__global__ void __launch_bounds__(128) k_prep_precheck(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+    PTF_WARP_ROUNDS(ws.n, m, valid) {
+        const int route = valid ? prep_item<NC, PRECHECK>(cp, ws, io, m) : 0;
+        warp_append(ws.cnt + Q_STAB, ws.q_stab, route == 1, (int32_t)m);
+        warp_append(ws.cnt + Q_SPLIT, ws.q_split, route == 2, (int32_t)m);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stability trial evaluation (reading R2 of tm): W = exp(lnW), c = W / sum W,
+// gt = ln W + ln phi(c) - d, tm = 1 + sum W (gt - 1).
+// ---------------------------------------------------------------------------
+template <int NC>
+__device__ __forceinline__ bool stab_eval(const Comp<NC>& cp, const Mix<NC>& mx, const double* d, const double* lnW,
+                                          double* W, double& Wt, double* c, Phase<NC>& ph, double* gt, double& tm) {
+    Wt = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        W[i] = exp(lnW[i]);
+        Wt += W[i];
+    }
+    double inv = 1.0 / Wt;
+#pragma unroll
+    for (int i = 0; i < NC; i++) c[i] = W[i] * inv;
+    eos<NC>(cp, mx, c, ph);
+    double t = 1.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        gt[i] = lnW[i] + ph.lnphi[i] - d[i];
+        t = fma(W[i], gt[i] - 1.0, t);
+    }
+    tm = t;
+    return isfinite(t);
+}
+
+// ---------------------------------------------------------------------------
+// Stability SS (Sec. 2.2.1, Eq. ss_analyser) with DEM; item = 2 q + trial.
+// ---------------------------------------------------------------------------
+// Returns true if the trial needs the trust region.
+template <int NC>
+__device__ __forceinline__ bool stab_ss_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t item) {
+    const int64_t n = ws.n;
+    bool need_tr = false;
+    {
+        {
+            const int64_t m = ws.q_stab[item >> 1];
+            const int t = (int)(item & 1);
+            Mix<NC> mx;
+            load_mix<NC>(ws, m, mx);
+            double d[NC], lnW[NC], lnKw[NC];
+            wilson<NC>(cp, io.P[m], io.T[m], lnKw);
+#pragma unroll
+            for (int i = 0; i < NC; i++) {
+                d[i] = ws.d[i * n + m];
+                double lz = ws.lnz[i * n + m];
+                lnW[i] = t == 0 ? lz + lnKw[i] : lz - lnKw[i];  // W = K z (vapour-like), z / K (liquid-like)
+            }
+            double W[NC], c[NC], gt[NC], Wt, tm = 0.0, res_prev = INFINITY;
+            double dp[NC], dp2[NC], lnWp[NC];
+#pragma unroll
+            for (int i = 0; i < NC; i++) dp[i] = dp2[i] = 0.0;
+            Phase<NC> ph;
+            int iters = 0, nonfinite = 0;
+            bool dem_pending = false, done = false;
+#pragma unroll 1
+            for (int it = 0;; it++) {
+                bool bad = !stab_eval<NC>(cp, mx, d, lnW, W, Wt, c, ph, gt, tm);
+                double res = bad ? INFINITY : maxabs<NC>(gt);
+                if (dem_pending && (bad || !(res < res_prev))) {
+                    dem_pending = false;
+#pragma unroll
+                    for (int i = 0; i < NC; i++) lnW[i] = lnWp[i];
+                    continue;
+                }
+                dem_pending = false;
+                if (bad) { nonfinite = 1; done = true; tm = NAN; break; }
+                if (tm < -kEpsNeg) { done = true; break; }
+                if (res < kTolStab) { done = true; break; }
+                if (it >= kSSStab) break;
+                double dk[NC];
+#pragma unroll
+                for (int i = 0; i < NC; i++) {
+                    dk[i] = -gt[i];
+                    lnW[i] += dk[i];
+                }
+                int s = iters + 1;
+                if (s % 5 == 0) {
+                    double f = dem_factor<NC>(dk, dp, dp2);
+                    if (f > 0.0) {
+#pragma unroll
+                        for (int i = 0; i < NC; i++) {
+                            lnWp[i] = lnW[i];
+                            lnW[i] += dk[i] * f;
+                        }
+                        dem_pending = true;
+                        res_prev = res;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < NC; i++) {
+                    dp2[i] = dp[i];
+                    dp[i] = dk[i];
+                }
+                iters = s;
+            }
+#pragma unroll
+            for (int i = 0; i < NC; i++) ws.lnW[(t * NC + i) * n + m] = lnW[i];
+            ws.tm[t * n + m] = tm;
+            ws.tflag[t * n + m] = iters | (done ? 0 : (1 << 16)) | (nonfinite << 18);
+            need_tr = !done;
+        }
+    }
+    return need_tr;
+}
+
+template <int NC>
+__global__ void __launch_bounds__(128) k_stab_ss(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+    const int64_t len = 2 * (int64_t)(*(volatile int32_t*)(ws.cnt + Q_STAB));
+    PTF_WARP_ROUNDS(len, item, valid) {
+        const bool need_tr = valid ? stab_ss_item<NC>(cp, ws, io, item) : false;
+        warp_append(ws.cnt + Q_STAB_TR, ws.q_stab_tr, need_tr, (int32_t)item);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stability trust region (Appendix B.1, Eqs. tr_sa, analysis_grad/hess).
+// ---------------------------------------------------------------------------
+template <int NC>
+struct StabPt {
+    double lnW[NC], gt[NC], g[NC], tm;
+    double H[NC * (NC + 1) / 2];
+};
+
+template <int NC>
+__device__ __forceinline__ bool stab_point(const Comp<NC>& cp, const Mix<NC>& mx, const double* d, StabPt<NC>& p) {
+    double W[NC], c[NC], Wt;
+    Phase<NC> ph;
+    if (!stab_eval<NC>(cp, mx, d, p.lnW, W, Wt, c, ph, p.gt, p.tm)) return false;
+    double J[NC * (NC + 1) / 2];
+    dlnphi_dn<NC>(cp, mx, c, ph, J);
+    double sW[NC], inv = 1.0 / Wt;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        sW[i] = sqrt(W[i]);
+        p.g[i] = sW[i] * p.gt[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NC; i++)
+#pragma unroll
+        for (int j = 0; j <= i; j++)
+            p.H[tri(i, j)] = sW[i] * sW[j] * J[tri(i, j)] * inv + (i == j ? 1.0 + 0.5 * p.gt[i] : 0.0);
+    return true;
+}
+
+template <int NC>
+__device__ __forceinline__ void stab_tr_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t item) {
+    const int64_t n = ws.n;
+    {
+        {
+            const int64_t m = ws.q_stab[item >> 1];
+            const int t = (int)(item & 1);
+            Mix<NC> mx;
+            load_mix<NC>(ws, m, mx);
+            double d[NC];
+            StabPt<NC> cur, nxt;
+#pragma unroll
+            for (int i = 0; i < NC; i++) {
+                d[i] = ws.d[i * n + m];
+                cur.lnW[i] = ws.lnW[(t * NC + i) * n + m];
+            }
+            int32_t fl = ws.tflag[t * n + m];
+            int iters = 0, maxiter = 0, nonfinite = 0;
+            double beta[NC], Lf[NC * (NC + 1) / 2], u[NC];
+            if (!stab_point<NC>(cp, mx, d, cur)) {
+                nonfinite = 1;
+                cur.tm = NAN;
+            } else {
+#pragma unroll
+                for (int i = 0; i < NC; i++) beta[i] = 2.0 * exp(0.5 * cur.lnW[i]);
+                double radius = -1.0;
+#pragma unroll 1
+                for (int it = 0;; it++) {
+                    if (cur.tm < -kEpsNeg) break;
+                    if (maxabs<NC>(cur.g) < kTolStab) break;
+                    if (it == kTRStab) { maxiter = 1; break; }
+                    if (radius < 0.0) {
+                        if (newton_scaled<NC>(cur.H, cur.g, Lf, u)) {
+                            double s = 0.0;
+                            for (int i = 0; i < NC; i++) s = fma(u[i], u[i], s);
+                            radius = sqrt(s);
+                        } else {
+                            radius = 1.0;
+                        }
+                    }
+                    tr_step_scaled<NC>(cur.H, cur.g, radius, Lf, u);
+                    double pred = 0.0;
+                    for (int i = 0; i < NC; i++) {
+                        double hd = 0.0;
+                        for (int j = 0; j < NC; j++) hd = fma(cur.H[i >= j ? tri(i, j) : tri(j, i)], u[j], hd);
+                        pred = fma(cur.g[i], u[i], fma(0.5 * u[i], hd, pred));
+                    }
+#pragma unroll
+                    for (int i = 0; i < NC; i++) nxt.lnW[i] = 2.0 * log(0.5 * fabs(beta[i] + u[i]));
+                    bool ok = stab_point<NC>(cp, mx, d, nxt);
+                    bool trusted = fabs(pred) > kPredTrust * (1.0 + fabs(cur.tm));
+                    double rho = !ok ? -1.0 : (trusted ? (nxt.tm - cur.tm) / pred : 0.5);
+                    if (rho > 0.0) {
+#pragma unroll
+                        for (int i = 0; i < NC; i++) beta[i] = fabs(beta[i] + u[i]);
+                        cur = nxt;
+                    }
+                    if (rho <= 0.25) radius *= 0.5;
+                    else if (rho >= 0.75) radius *= 2.0;
+                    iters = it + 1;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NC; i++) ws.lnW[(t * NC + i) * n + m] = cur.lnW[i];
+            ws.tm[t * n + m] = cur.tm;
+            ws.tflag[t * n + m] = (fl & 0xff) | (iters << 8) | (1 << 16) | (maxiter << 17) | (nonfinite << 18);
+        }
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(128) k_stab_tr(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+    const int64_t len = *(volatile int32_t*)(ws.cnt + Q_STAB_TR);
+    PTF_WARP_ROUNDS(len, qi, valid) {
+        if (valid) stab_tr_item<NC>(cp, ws, io, ws.q_stab_tr[qi]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stability decision and K re-estimate (Sec. 2.2.1, last sentence).
+// ---------------------------------------------------------------------------
+// Returns true if the mixture goes to the split queue.
+template <int NC>
+__device__ __forceinline__ bool stab_decide_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t m) {
+    const int64_t n = ws.n;
+    bool to_split = false;
+    {
+        {
+            const double tv = ws.tm[m], tl = ws.tm[n + m];
+            const int32_t fv = ws.tflag[m], fl = ws.tflag[n + m];
+            int32_t st = io.status[m];
+            if ((fv | fl) & (1 << 16)) st |= ST_STAB_TR;
+            if ((fv | fl) & (1 << 17)) st |= ST_MAXITER;
+            if (io.iters)
+                io.iters[m] = ((((fv & 0xff) + (fl & 0xff)) & 0xff) << 16) |
+                              (((((fv >> 8) & 0xff) + ((fl >> 8) & 0xff)) & 0xff) << 24);
+            double z[NC];
+#pragma unroll
+            for (int i = 0; i < NC; i++) z[i] = io.z[i * io.ld + m];
+            if ((fv | fl) & (1 << 18)) {
+                st |= ST_NONFINITE;
+                write_single<NC>(io, m, z);
+            } else {
+                double tmin = tv < tl ? tv : tl;
+                if (!(tmin < -kEpsNeg)) {
+                    write_single<NC>(io, m, z);
+                } else {
+                    const int t = tl < tv ? 1 : 0;
+#pragma unroll
+                    for (int i = 0; i < NC; i++) {
+                        double lz = ws.lnz[i * n + m], lw = ws.lnW[(t * NC + i) * n + m];
+                        ws.lnK[i * n + m] = t == 1 ? lz - lw : lw - lz;
+                    }
+                    to_split = true;
+                }
+            }
+            io.status[m] = st;
+        }
+    }
+    return to_split;
+}
+
+template <int NC>
+__global__ void __launch_bounds__(128) k_stab_decide(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+    const int64_t len = *(volatile int32_t*)(ws.cnt + Q_STAB);
+    PTF_WARP_ROUNDS(len, qi, valid) {
+        const int64_t m = valid ? ws.q_stab[qi] : 0;
+        const bool to_split = valid ? stab_decide_item<NC>(cp, ws, io, m) : false;
+        warp_append(ws.cnt + Q_SPLIT, ws.q_split, to_split, (int32_t)m);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Phase-split SS (Sec. 2.2.2) with DEM, convergence at the fugacity residual.
+// ---------------------------------------------------------------------------
+// Returns true if the split needs the trust region.
+template <int NC>
+__device__ __forceinline__ bool split_ss_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t m) {
+    const int64_t n = ws.n;
+    bool need_tr = false;
+    {
+        {
+            Mix<NC> mx;
+            load_mix<NC>(ws, m, mx);
+            double z[NC], lnK[NC], K[NC], t[NC], x[NC], y[NC], gt[NC];
+            double dp[NC], dp2[NC], lnKp[NC];
+#pragma unroll
+            for (int i = 0; i < NC; i++) {
+                z[i] = io.z[i * io.ld + m];
+                lnK[i] = ws.lnK[i * n + m];
+                dp[i] = dp2[i] = 0.0;
+            }
+            int32_t st = io.status[m];
+            Phase<NC> pl, pv;
+            double th = 0.5, res_prev = INFINITY;
+            int iters = 0;
+            bool dem_pending = false;
+            int outcome = 0;  // 0 -> TR, 1 converged, 2 collapse, 3 nonfinite
+#pragma unroll 1
+            for (int it = 0;; it++) {
+                int fail = 0;
+                double res = INFINITY;
+                if (maxabs<NC>(lnK) < kTrivialLnK) fail = 1;
+                if (!fail) {
+#pragma unroll
+                    for (int i = 0; i < NC; i++) K[i] = exp(lnK[i]);
+                    if (!rachford_rice<NC>(z, K, th, t)) fail = 1;
+                }
+                if (!fail) {
+#pragma unroll
+                    for (int i = 0; i < NC; i++) {
+                        x[i] = z[i] * t[i];
+                        y[i] = K[i] * x[i];
+                    }
+                    eos<NC>(cp, mx, x, pl);
+                    eos<NC>(cp, mx, y, pv);
+#pragma unroll
+                    for (int i = 0; i < NC; i++) gt[i] = lnK[i] + pv.lnphi[i] - pl.lnphi[i];
+                    res = maxabs<NC>(gt);
+                    if (!(res < INFINITY)) fail = 2;
+                }
+                if (dem_pending && (fail || !(res < res_prev))) {
+                    dem_pending = false;
+#pragma unroll
+                    for (int i = 0; i < NC; i++) lnK[i] = lnKp[i];
+                    continue;
+                }
+                dem_pending = false;
+                if (fail == 1) { outcome = 2; break; }
+                if (fail == 2) { outcome = 3; break; }
+                if (res <= kTolFug) { outcome = (th > 0.0 && th < 1.0) ? 1 : 2; break; }
+                if (it >= kSSSplit) break;
+                double dk[NC];
+#pragma unroll
+                for (int i = 0; i < NC; i++) {
+                    dk[i] = -gt[i];
+                    lnK[i] += dk[i];
+                }
+                int s = iters + 1;
+                if (s % 5 == 0) {
+                    double f = dem_factor<NC>(dk, dp, dp2);
+                    if (f > 0.0) {
+#pragma unroll
+                        for (int i = 0; i < NC; i++) {
+                            lnKp[i] = lnK[i];
+                            lnK[i] += dk[i] * f;
+                        }
+                        dem_pending = true;
+                        res_prev = res;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < NC; i++) {
+                    dp2[i] = dp[i];
+                    dp[i] = dk[i];
+                }
+                iters = s;
+            }
+            if (outcome == 1) {
+                write_two<NC>(io, m, th, x, y, pl.Z, pv.Z);
+            } else if (outcome == 2) {
+                st |= ST_COLLAPSE;
+                write_single<NC>(io, m, z);
+            } else if (outcome == 3) {
+                st |= ST_NONFINITE;
+                write_single<NC>(io, m, z);
+            } else {
+                // trust-region start: the last evaluated SS point, or the
+                // material-balance point at theta = 1/2 for a negative flash
+                st |= ST_SPLIT_TR;
+                const bool inside = th > 0.0 && th < 1.0;
+#pragma unroll
+                for (int i = 0; i < NC; i++)
+                    ws.nV[i * n + m] = inside ? th * y[i] : 0.5 * K[i] * z[i] / (1.0 + 0.5 * (K[i] - 1.0));
+                need_tr = true;
+            }
+            io.status[m] = st;
+            if (io.iters) io.iters[m] = (io.iters[m] & ~0xff) | (iters & 0xff);
+        }
+    }
+    return need_tr;
+}
+
+template <int NC>
+__global__ void __launch_bounds__(128) k_split_ss(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+    const int64_t len = *(volatile int32_t*)(ws.cnt + Q_SPLIT);
+    PTF_WARP_ROUNDS(len, qi, valid) {
+        const int64_t m = valid ? ws.q_split[qi] : 0;
+        const bool need_tr = valid ? split_ss_item<NC>(cp, ws, io, m) : false;
+        warp_append(ws.cnt + Q_SPLIT_TR, ws.q_split_tr, need_tr, (int32_t)m);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Phase-split trust region (Appendix B.2, Eqs. newton_splitter, split_grad,
+// split_hess) in the scaled variable u = D^{1/2} dn^V, D = diag(z / (x y)).
+// ---------------------------------------------------------------------------
+template <int NC>
+struct SplitPt {
+    double th, x[NC], y[NC], gt[NC], gs[NC], S[NC], G, ZL, ZV;
+    double Hs[NC * (NC + 1) / 2];  // S H S
+};
+
+template <int NC>
+__device__ __forceinline__ bool split_point(const Comp<NC>& cp, const Mix<NC>& mx, const double* z, const double* nV,
+                                            SplitPt<NC>& p) {
+    double th = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) th += nV[i];
+    p.th = th;
+    const double iv = 1.0 / th, il = 1.0 / (1.0 - th);
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        p.y[i] = nV[i] * iv;
+        p.x[i] = (z[i] - nV[i]) * il;
+    }
+    Phase<NC> pl, pv;
+    eos<NC>(cp, mx, p.x, pl);
+    eos<NC>(cp, mx, p.y, pv);
+    p.ZL = pl.Z;
+    p.ZV = pv.Z;
+    double JL[NC * (NC + 1) / 2], JV[NC * (NC + 1) / 2];
+    dlnphi_dn<NC>(cp, mx, p.x, pl, JL);
+    dlnphi_dn<NC>(cp, mx, p.y, pv, JV);
+    double G = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        double mul = log(p.x[i]) + pl.lnphi[i], muv = log(p.y[i]) + pv.lnphi[i];
+        p.gt[i] = muv - mul;
+        G = fma(z[i] - nV[i], mul, fma(nV[i], muv, G));
+    }
+    p.G = G;
+    const double w = 1.0 / (th * (1.0 - th));
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        double md = z[i] / (p.x[i] * p.y[i]);
+        p.S[i] = 1.0 / sqrt(md);
+        p.gs[i] = p.S[i] * p.gt[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NC; i++)
+#pragma unroll
+        for (int j = 0; j <= i; j++) {
+            double h = th * JL[tri(i, j)] + (1.0 - th) * JV[tri(i, j)] - 1.0;
+            if (i == j) h += z[i] / (p.x[i] * p.y[i]);
+            p.Hs[tri(i, j)] = w * h * p.S[i] * p.S[j];
+        }
+    return isfinite(G);
+}
+
+// 0.99 fraction-to-boundary cut keeping 0 < n^V_i + d_i < z_i
+template <int NC>
+__device__ __forceinline__ double boundary_cut(const double* z, const double* nV, const double* d) {
+    double tau = 1.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        if (d[i] < 0.0) tau = fmin(tau, 0.99 * nV[i] / (-d[i]));
+        else if (d[i] > 0.0) tau = fmin(tau, 0.99 * (z[i] - nV[i]) / d[i]);
+    }
+    return tau;
+}
+
+template <int NC>
+__device__ __forceinline__ void split_tr_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t m) {
+    const int64_t n = ws.n;
+    {
+        {
+            Mix<NC> mx;
+            load_mix<NC>(ws, m, mx);
+            double z[NC], nV[NC];
+#pragma unroll
+            for (int i = 0; i < NC; i++) {
+                z[i] = io.z[i * io.ld + m];
+                nV[i] = ws.nV[i * n + m];
+            }
+            int32_t st = io.status[m];
+            SplitPt<NC> cur, nxt;
+            double Lf[NC * (NC + 1) / 2], u[NC], dstep[NC];
+            int iters = 0;
+            bool nonfinite = !split_point<NC>(cp, mx, z, nV, cur);
+            if (!nonfinite) {
+                double radius = -1.0;
+                int it = 0, newton_steps = 0;
+                bool phase_newton = false;
+#pragma unroll 1
+                for (int guard = 0; guard < 64; guard++) {
+                    double res = maxabs<NC>(cur.gt);
+                    if (phase_newton) {
+                        if (res <= kTolFug && newton_steps >= 1) break;
+                        if (newton_steps == kNewtonPolish) { st |= ST_MAXITER; break; }
+                    } else if (res < kTolSplitTR) {
+                        phase_newton = true;
+                        continue;
+                    }
+                    if (!phase_newton && it == kTRSplit) { st |= ST_MAXITER; break; }
+                    if (phase_newton) {
+                        if (!newton_scaled<NC>(cur.Hs, cur.gs, Lf, u)) {
+                            if (res > kTolFug) st |= ST_MAXITER;
+                            break;
+                        }
+#pragma unroll
+                        for (int i = 0; i < NC; i++) dstep[i] = cur.S[i] * u[i];
+                        double tau = boundary_cut<NC>(z, nV, dstep);
+#pragma unroll
+                        for (int i = 0; i < NC; i++) nV[i] += tau * dstep[i];
+                        if (!split_point<NC>(cp, mx, z, nV, cur)) { nonfinite = true; break; }
+                        newton_steps++;
+                        iters++;
+                        continue;
+                    }
+                    if (radius < 0.0) {
+                        if (newton_scaled<NC>(cur.Hs, cur.gs, Lf, u)) {
+                            double s = 0.0;
+                            for (int i = 0; i < NC; i++) s = fma(u[i], u[i], s);
+                            radius = sqrt(s);
+                        } else {
+                            radius = 1.0;
+                        }
+                    }
+                    tr_step_scaled<NC>(cur.Hs, cur.gs, radius, Lf, u);
+#pragma unroll
+                    for (int i = 0; i < NC; i++) dstep[i] = cur.S[i] * u[i];
+                    double tau = boundary_cut<NC>(z, nV, dstep);
+                    if (tau < 1.0) {
+#pragma unroll
+                        for (int i = 0; i < NC; i++) {
+                            u[i] *= tau;
+                            dstep[i] *= tau;
+                        }
+                    }
+                    double pred = 0.0;
+                    for (int i = 0; i < NC; i++) {
+                        double hd = 0.0;
+                        for (int j = 0; j < NC; j++) hd = fma(cur.Hs[i >= j ? tri(i, j) : tri(j, i)], u[j], hd);
+                        pred = fma(cur.gs[i], u[i], fma(0.5 * u[i], hd, pred));
+                    }
+                    double nVn[NC];
+#pragma unroll
+                    for (int i = 0; i < NC; i++) nVn[i] = nV[i] + dstep[i];
+                    bool ok = split_point<NC>(cp, mx, z, nVn, nxt);
+                    bool trusted = fabs(pred) > kPredTrust * (1.0 + fabs(cur.G));
+                    double rho = !ok ? -1.0 : (trusted ? (nxt.G - cur.G) / pred : 0.5);
+                    if (rho > 0.0) {
+#pragma unroll
+                        for (int i = 0; i < NC; i++) nV[i] = nVn[i];
+                        cur = nxt;
+                    }
+                    if (rho <= 0.25) radius *= 0.5;
+                    else if (rho >= 0.75) radius *= 2.0;
+                    it++;
+                    iters = it;
+                }
+            }
+            if (nonfinite) {
+                st |= ST_NONFINITE;
+                write_single<NC>(io, m, z);
+            } else if (!(cur.th > 0.0 && cur.th < 1.0)) {
+                st |= ST_COLLAPSE;
+                write_single<NC>(io, m, z);
+            } else {
+                write_two<NC>(io, m, cur.th, cur.x, cur.y, cur.ZL, cur.ZV);
+            }
+            io.status[m] = st;
+            if (io.iters) io.iters[m] = (io.iters[m] & ~0xff00) | ((iters & 0xff) << 8);
+        }
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(128) k_split_tr(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+    const int64_t len = *(volatile int32_t*)(ws.cnt + Q_SPLIT_TR);
+    PTF_WARP_ROUNDS(len, qi, valid) {
+        if (valid) split_tr_item<NC>(cp, ws, io, ws.q_split_tr[qi]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stability-only outputs (ptflash_stability): io.nphase = stable flag,
+// io.beta = min tm, io.K = K re-estimate.
+// ---------------------------------------------------------------------------
+template <int NC>
+__device__ __forceinline__ void stab_out_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t m) {
+    const int64_t n = ws.n;
+    {
+        {
+            const double tv = ws.tm[m], tl = ws.tm[n + m];
+            const int32_t fv = ws.tflag[m], fl = ws.tflag[n + m];
+            int32_t st = io.status[m];
+            if ((fv | fl) & (1 << 16)) st |= ST_STAB_TR;
+            if ((fv | fl) & (1 << 17)) st |= ST_MAXITER;
+            if ((fv | fl) & (1 << 18)) st |= ST_NONFINITE;
+            const double tmin = tv < tl ? tv : tl;
+            io.nphase[m] = (tmin < -kEpsNeg) ? 0 : 1;
+            io.beta[m] = tmin;
+            const int t = tl < tv ? 1 : 0;
+#pragma unroll
+            for (int i = 0; i < NC; i++) {
+                double lz = ws.lnz[i * n + m], lw = ws.lnW[(t * NC + i) * n + m];
+                io.K[i * io.ld + m] = exp(t == 1 ? lz - lw : lw - lz);
+            }
+            io.status[m] = st;
+        }
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(128) k_stab_out(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+    const int64_t len = *(volatile int32_t*)(ws.cnt + Q_STAB);
+    PTF_WARP_ROUNDS(len, qi, valid) {
+        if (valid) stab_out_item<NC>(cp, ws, io, ws.q_stab[qi]);
+    }
+}
+
+}  // namespace ptf

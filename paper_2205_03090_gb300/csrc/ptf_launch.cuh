@@ -1,0 +1,54 @@
+// ptf_launch.cuh -- host-side launch sequences, one instantiation per NC.
+#pragma once
+#include <cmath>
+#include "ptf_kernels.cuh"
+#include "ptf_comp.cuh"
+
+namespace ptf {
+
+// Stage order of the timing events: prep(+precheck), stability SS,
+// stability TR, decide (or stability output), split SS, split TR.
+constexpr int kStages = 6;
+
+// mode 0: plain flash; mode 1: stability only.  ev (optional, kStages + 1
+// events) is recorded before each stage kernel and after the last one.
+template <int NC>
+cudaError_t launch_plain(const CompHost& h, const WS& ws, const IO& io, int grid, int mode, cudaStream_t s,
+                         cudaEvent_t* ev) {
+    const Comp<NC> cp = make_comp<NC>(h);
+    auto mark = [&](int k) {
+        if (ev) cudaEventRecord(ev[k], s);
+    };
+    mark(0);
+    if (mode == 0) k_prep_precheck<NC, true><<<grid, 128, 0, s>>>(cp, ws, io);
+    else k_prep_precheck<NC, false><<<grid, 128, 0, s>>>(cp, ws, io);
+    mark(1);
+    k_stab_ss<NC><<<grid, 128, 0, s>>>(cp, ws, io);
+    mark(2);
+    k_stab_tr<NC><<<grid, 128, 0, s>>>(cp, ws, io);
+    mark(3);
+    if (mode == 0) k_stab_decide<NC><<<grid, 128, 0, s>>>(cp, ws, io);
+    else k_stab_out<NC><<<grid, 128, 0, s>>>(cp, ws, io);
+    mark(4);
+    if (mode == 0) {
+        k_split_ss<NC><<<grid, 128, 0, s>>>(cp, ws, io);
+        mark(5);
+        k_split_tr<NC><<<grid, 128, 0, s>>>(cp, ws, io);
+        mark(6);
+    } else {
+        mark(5);
+        mark(6);
+    }
+    return cudaGetLastError();
+}
+
+// explicit instantiations live in ptf_inst_*.cu
+#define PTF_DECLARE_NC(NC) \
+    extern template cudaError_t launch_plain<NC>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, \
+                                                 cudaEvent_t*);
+PTF_DECLARE_NC(2) PTF_DECLARE_NC(3) PTF_DECLARE_NC(4) PTF_DECLARE_NC(5) PTF_DECLARE_NC(6) PTF_DECLARE_NC(7)
+PTF_DECLARE_NC(8) PTF_DECLARE_NC(9) PTF_DECLARE_NC(10) PTF_DECLARE_NC(11) PTF_DECLARE_NC(12) PTF_DECLARE_NC(13)
+PTF_DECLARE_NC(14) PTF_DECLARE_NC(15) PTF_DECLARE_NC(16)
+#undef PTF_DECLARE_NC
+
+}  // namespace ptf

@@ -1,0 +1,198 @@
+"""Thin Python binding of the C ABI in include/ptflash.h.
+
+Argument marshalling only: every step of the flash runs in the CUDA library
+(_build/libptflash.so).  torch supplies device memory and streams.  There is
+no CPU fallback -- if the library is missing or CUDA is unavailable, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libptflash.so")
+
+PTF_ST_PRECHECK_UNSTABLE = 1
+PTF_ST_STAB_RUN = 2
+PTF_ST_STAB_TR = 4
+PTF_ST_SPLIT_TR = 8
+PTF_ST_MAXITER = 16
+PTF_ST_COLLAPSE = 32
+PTF_ST_NONFINITE = 64
+PTF_ST_NN_STABLE = 128
+PTF_ST_NN_UNSTABLE = 256
+PTF_ST_NN_INIT = 512
+
+_lib = None
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+class PtflashError(RuntimeError):
+    pass
+
+
+class ptflash_options(ctypes.Structure):
+    _fields_ = [("use_nn", ctypes.c_int32), ("p_l", ctypes.c_double), ("p_r", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise PtflashError(f"CUDA library not built: {path} (run paper_2205_03090_gb300/build.py)")
+    lib = ctypes.CDLL(path)
+    lib.ptflash_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, _I64]
+    lib.ptflash_destroy.argtypes = [_VP]
+    lib.ptflash_set_components.argtypes = [_VP, ctypes.c_int, _D, _D, _D, _D]
+    dev = [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ptflash_options), _VP]
+    lib.ptflash_flash.argtypes = dev
+    lib.ptflash_flash_host.argtypes = dev
+    lib.ptflash_stability.argtypes = [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]
+    lib.ptflash_last_counts.argtypes = [_VP, ctypes.POINTER(_I64)]
+    lib.ptflash_set_profiling.argtypes = [_VP, ctypes.c_int]
+    lib.ptflash_last_stage_ms.argtypes = [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    lib.ptflash_strerror.argtypes = [ctypes.c_int]
+    lib.ptflash_strerror.restype = ctypes.c_char_p
+    lib.ptflash_last_cuda_error.restype = ctypes.c_char_p
+    for f in ("ptflash_create", "ptflash_destroy", "ptflash_set_components", "ptflash_flash", "ptflash_flash_host",
+              "ptflash_stability", "ptflash_last_counts", "ptflash_set_profiling", "ptflash_last_stage_ms"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        lib = load()
+        msg = lib.ptflash_strerror(rc).decode()
+        cuda = lib.ptflash_last_cuda_error().decode()
+        raise PtflashError(f"ptflash error {rc}: {msg}" + (f" ({cuda})" if cuda else ""))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _opts(use_nn=False, p_l=0.02, p_r=0.98):
+    o = ptflash_options()
+    o.use_nn = 1 if use_nn else 0
+    o.p_l = p_l
+    o.p_r = p_r
+    return o
+
+
+@dataclass
+class FlashResult:
+    nphase: "object"
+    beta: "object"
+    x: "object"
+    y: "object"
+    K: "object"
+    status: "object"
+    iters: "object"
+
+
+class Flash:
+    """A flash context on the current CUDA device (ptflash_create / set_components)."""
+
+    def __init__(self, Tc, Pc, omega, kij, n_max: int = 1 << 20, nc_max: int | None = None):
+        lib = load()
+        Tc = np.ascontiguousarray(Tc, np.float64)
+        nc = int(Tc.shape[0])
+        self.nc = nc
+        self.n_max = int(n_max)
+        h = _VP()
+        _check(lib.ptflash_create(ctypes.byref(h), nc_max or nc, self.n_max))
+        self._h = h
+        arrs = [Tc, np.ascontiguousarray(Pc, np.float64), np.ascontiguousarray(omega, np.float64),
+                np.ascontiguousarray(kij, np.float64).reshape(-1)]
+        _check(lib.ptflash_set_components(h, nc, *[a.ctypes.data_as(_D) for a in arrs]))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ptflash_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def alloc_outputs(self, n: int, device="cuda", with_iters=True):
+        import torch
+        f64 = dict(dtype=torch.float64, device=device)
+        i32 = dict(dtype=torch.int32, device=device)
+        return FlashResult(torch.empty(n, **i32), torch.empty(n, **f64), torch.empty(self.nc, n, **f64),
+                           torch.empty(self.nc, n, **f64), torch.empty(self.nc, n, **f64), torch.empty(n, **i32),
+                           torch.empty(n, **i32) if with_iters else None)
+
+    def ptflash_flash(self, P, T, z, out: FlashResult | None = None, use_nn=False, p_l=0.02, p_r=0.98,
+                      stream=None) -> FlashResult:
+        """Device tensors P[n], T[n], z[nc, n] (float64, contiguous)."""
+        n = int(P.shape[0])
+        assert z.shape == (self.nc, n) and P.is_cuda and z.is_contiguous()
+        out = out or self.alloc_outputs(n, P.device)
+        o = _opts(use_nn, p_l, p_r)
+        _check(load().ptflash_flash(self._h, n, _ptr(P), _ptr(T), _ptr(z), _ptr(out.nphase), _ptr(out.beta),
+                                    _ptr(out.x), _ptr(out.y), _ptr(out.K), _ptr(out.status), _ptr(out.iters),
+                                    ctypes.byref(o), _stream_handle(stream)))
+        return out
+
+    def ptflash_flash_host(self, P, T, z, out=None, use_nn=False, p_l=0.02, p_r=0.98, stream=None):
+        """Host tensors (pinned CPU torch tensors or NumPy arrays); returns host outputs."""
+        import torch
+        n = int(P.shape[0])
+        if out is None:
+            out = FlashResult(torch.empty(n, dtype=torch.int32), torch.empty(n, dtype=torch.float64),
+                              torch.empty(self.nc, n, dtype=torch.float64),
+                              torch.empty(self.nc, n, dtype=torch.float64),
+                              torch.empty(self.nc, n, dtype=torch.float64), torch.empty(n, dtype=torch.int32),
+                              torch.empty(n, dtype=torch.int32))
+        o = _opts(use_nn, p_l, p_r)
+        _check(load().ptflash_flash_host(self._h, n, _ptr(P), _ptr(T), _ptr(z), _ptr(out.nphase), _ptr(out.beta),
+                                         _ptr(out.x), _ptr(out.y), _ptr(out.K), _ptr(out.status), _ptr(out.iters),
+                                         ctypes.byref(o), _stream_handle(stream)))
+        return out
+
+    def ptflash_stability(self, P, T, z, stream=None):
+        import torch
+        n = int(P.shape[0])
+        dev = P.device
+        stable = torch.empty(n, dtype=torch.int32, device=dev)
+        tm = torch.empty(n, dtype=torch.float64, device=dev)
+        K = torch.empty(self.nc, n, dtype=torch.float64, device=dev)
+        status = torch.empty(n, dtype=torch.int32, device=dev)
+        _check(load().ptflash_stability(self._h, n, _ptr(P), _ptr(T), _ptr(z), _ptr(stable), _ptr(tm), _ptr(K),
+                                        _ptr(status), _stream_handle(stream)))
+        return stable, tm, K, status
+
+    STAGES = ("prep_precheck", "stab_ss", "stab_tr", "stab_decide", "split_ss", "split_tr")
+
+    def ptflash_set_profiling(self, enable: bool = True):
+        _check(load().ptflash_set_profiling(self._h, 1 if enable else 0))
+
+    def ptflash_last_stage_ms(self):
+        ms = (ctypes.c_double * 6)()
+        _check(load().ptflash_last_stage_ms(self._h, ms, 6))
+        return dict(zip(self.STAGES, list(ms)))
+
+    def ptflash_last_counts(self):
+        c = (_I64 * 4)()
+        _check(load().ptflash_last_counts(self._h, c))
+        return dict(stab=c[0], split=c[1], stab_tr=c[2], split_tr=c[3])

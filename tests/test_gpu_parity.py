@@ -1,0 +1,235 @@
+"""Parity of the CUDA flash (through the C ABI) with the CPU oracle.
+
+Tolerances (fixed by the method's accuracy target): the phase label must be
+identical wherever the oracle's fully converged min tpd satisfies
+|tpd| > 1e-8; where both sides report two phases, |d beta|, |d x|, |d y|
+<= 1e-8; every GPU two-phase result has fugacity residual <= 1e-10 when its
+x and y are re-evaluated by the oracle's EOS, and satisfies the material
+balance.
+"""
+import numpy as np
+import pytest
+
+from paper_2205_03090_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-8
+TOL_FUG = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ptf():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2205_03090_gb300 import build, ptflash
+    build.build()
+    ptflash.load()
+    return ptflash
+
+
+def _to_dev(cond):
+    import torch
+    return (torch.tensor(cond.P, device="cuda"), torch.tensor(cond.T, device="cuda"),
+            torch.tensor(cond.z, device="cuda").contiguous())
+
+
+def _gpu_flash(ptf, comp, cond, n_max=1 << 20):
+    import torch
+    fl = ptf.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=n_max)
+    P, T, z = _to_dev(cond)
+    out = fl.ptflash_flash(P, T, z)
+    torch.cuda.synchronize()
+    res = {k: getattr(out, k).cpu().numpy() for k in ("nphase", "beta", "x", "y", "K", "status", "iters")}
+    res["counts"] = fl.ptflash_last_counts()
+    fl.close()
+    return res
+
+
+def _fug_residual(oracle_mod, s, P, T, x, y):
+    _, lx = oracle_mod.eos(s, P, T, x)
+    _, ly = oracle_mod.eos(s, P, T, y)
+    return np.abs(np.log(y) + ly - np.log(x) - lx).max()
+
+
+def compare(oracle_mod, comp, cond, g, idx=None, fug_checks=400):
+    """Compare GPU results g (all n) with the oracle on indices idx."""
+    s = oracle_mod.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
+    if idx is None:
+        idx = np.arange(cond.n)
+    P, T, z = cond.P[idx], cond.T[idx], np.ascontiguousarray(cond.z[:, idx])
+    o = oracle_mod.flash(s, P, T, z)
+    tp = oracle_mod.tpd_min(s, P, T, z)
+    gn, gb, gx, gy = g["nphase"][idx], g["beta"][idx], g["x"][:, idx], g["y"][:, idx]
+    graded = np.abs(tp) > 1e-8
+    lab_bad = graded & (gn != o["nphase"])
+    both = (gn == 2) & (o["nphase"] == 2)
+    db = np.abs(gb - o["beta"])
+    dx = np.abs(gx - o["x"]).max(axis=0)
+    dy = np.abs(gy - o["y"]).max(axis=0)
+    val_bad = both & ((db > TOL) | (dx > TOL) | (dy > TOL))
+    # GPU two-phase results must be equilibria: material balance and fugacity
+    two = np.nonzero(gn == 2)[0]
+    mb = np.abs(gx[:, two] * (1 - gb[two]) + gy[:, two] * gb[two] - z[:, two]).max() if len(two) else 0.0
+    fres = [_fug_residual(oracle_mod, s, P[k], T[k], gx[:, k], gy[:, k]) for k in two[:fug_checks]
+            if not (g["status"][idx][k] & 16)]
+    route_mask = 1 | 2  # precheck-unstable / stability-run routing bits
+    route_same = ((g["status"][idx] & route_mask) == (o["status"] & route_mask)).mean()
+    return dict(n=len(idx), graded=int(graded.sum()), label_bad=int(lab_bad.sum()), both=int(both.sum()),
+                val_bad=int(val_bad.sum()), max_db=float(db[both].max()) if both.any() else 0.0,
+                max_dx=float(dx[both].max()) if both.any() else 0.0,
+                max_dy=float(dy[both].max()) if both.any() else 0.0, mass_balance=float(mb),
+                max_fug=float(max(fres)) if fres else 0.0, route_same=float(route_same),
+                bad_idx=np.nonzero(lab_bad | val_bad)[0])
+
+
+def _assert_parity(r, max_val_bad_frac=0.0):
+    assert r["label_bad"] == 0, r
+    assert r["val_bad"] <= max_val_bad_frac * max(1, r["both"]), r
+    assert r["mass_balance"] < 1e-12, r
+    assert r["max_fug"] <= TOL_FUG, r
+    assert r["route_same"] > 0.999, r
+
+
+def test_parity_nc3_full(ptf, oracle_mod):
+    """3 pseudo-components, 1e4 mixtures: every mixture compared."""
+    comp, cond = wl.workload("nc3_1e4")
+    g = _gpu_flash(ptf, comp, cond)
+    r = compare(oracle_mod, comp, cond, g)
+    print("nc3", {k: v for k, v in r.items() if k != "bad_idx"})
+    _assert_parity(r)
+
+
+def test_parity_nc8_subset(ptf, oracle_mod):
+    """8 pseudo-components (Dirichlet 0.5): 20000 mixtures, several tiles and
+    a ragged tail (20000 is not a multiple of the 128-thread block)."""
+    comp, cond = wl.workload("nc8_1e6", 20000)
+    g = _gpu_flash(ptf, comp, cond)
+    r = compare(oracle_mod, comp, cond, g)
+    print("nc8", {k: v for k, v in r.items() if k != "bad_idx"})
+    _assert_parity(r, max_val_bad_frac=1e-3)
+
+
+def test_parity_nc10_subset(ptf, oracle_mod):
+    comp, cond = wl.workload("nc10_2phase_1e6", 8000)
+    g = _gpu_flash(ptf, comp, cond)
+    r = compare(oracle_mod, comp, cond, g)
+    print("nc10", {k: v for k, v in r.items() if k != "bad_idx"})
+    _assert_parity(r, max_val_bad_frac=1e-3)
+
+
+def test_parity_full_size_sampled(ptf, oracle_mod):
+    """The 8-component, 1e6-mixture workload in the launch configuration the
+    benchmark times; 3000 sampled outputs recomputed by the oracle."""
+    comp, cond = wl.workload("nc8_1e6")
+    g = _gpu_flash(ptf, comp, cond)
+    rng = np.random.default_rng(123)
+    idx = np.sort(rng.choice(cond.n, 3000, replace=False))
+    r = compare(oracle_mod, comp, cond, g, idx=idx)
+    print("nc8 full sampled", {k: v for k, v in r.items() if k != "bad_idx"}, g["counts"])
+    _assert_parity(r, max_val_bad_frac=1e-3)
+    # properties that hold at any size: statuses finite, outputs finite
+    assert (g["status"] & 64).sum() == 0
+    assert np.isfinite(g["beta"]).all() and np.isfinite(g["x"]).all()
+
+
+def test_chunked_equals_single_launch(ptf):
+    """A batch larger than the context's n_max is processed in chunks with the
+    same results."""
+    comp, cond = wl.workload("nc8_1e6", 5000)
+    a = _gpu_flash(ptf, comp, cond, n_max=1 << 20)
+    b = _gpu_flash(ptf, comp, cond, n_max=1234)
+    for k in ("nphase", "status", "iters"):
+        np.testing.assert_array_equal(a[k], b[k])
+    for k in ("beta", "x", "y", "K"):
+        np.testing.assert_array_equal(a[k], b[k])
+    assert a["counts"] == b["counts"]
+
+
+def test_edge_cases(ptf, oracle_mod):
+    import torch
+    comp = wl.pseudo_components(4, 2)
+    fl = ptf.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=4096)
+    # empty batch is a no-op
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    fl.ptflash_flash(e, e, torch.empty(4, 0, dtype=torch.float64, device="cuda"))
+    # single mixture, pure-ish feeds, a non-positive pressure
+    z = np.full((4, 6), 1e-12)
+    for i in range(4):
+        z[i, i] = 1 - 3e-12
+    z[:, 4] = [0.25, 0.25, 0.25, 0.25]
+    z[:, 5] = [0.25, 0.25, 0.25, 0.25]
+    P = np.array([5.0, 5.0, 5.0, 5.0, 5.0, 0.0])
+    T = np.array([400.0] * 6)
+    out = fl.ptflash_flash(torch.tensor(P, device="cuda"), torch.tensor(T, device="cuda"),
+                           torch.tensor(z, device="cuda"))
+    torch.cuda.synchronize()
+    nph, st = out.nphase.cpu().numpy(), out.status.cpu().numpy()
+    assert np.all(nph[:4] == 1)
+    assert st[5] & 64 and nph[5] == 1  # P = 0 -> non-finite status, single phase
+    s = oracle_mod.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
+    o = oracle_mod.flash(s, P[:5], T[:5], z[:, :5])
+    np.testing.assert_array_equal(nph[:5], o["nphase"])
+    one = fl.ptflash_flash(torch.tensor(P[4:5], device="cuda"), torch.tensor(T[4:5], device="cuda"),
+                           torch.tensor(np.ascontiguousarray(z[:, 4:5]), device="cuda"))
+    torch.cuda.synchronize()
+    assert int(one.nphase.cpu()[0]) == int(o["nphase"][4])
+    fl.close()
+
+
+def test_host_entry_point_matches_device(ptf):
+    import torch
+    comp, cond = wl.workload("nc3_1e4", 3000)
+    fl = ptf.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=1000)
+    P, T, z = _to_dev(cond)
+    d = fl.ptflash_flash(P, T, z)
+    h = fl.ptflash_flash_host(torch.tensor(cond.P).pin_memory(), torch.tensor(cond.T).pin_memory(),
+                              torch.tensor(cond.z).pin_memory())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(d.nphase.cpu().numpy(), h.nphase.numpy())
+    np.testing.assert_array_equal(d.beta.cpu().numpy(), h.beta.numpy())
+    np.testing.assert_array_equal(d.x.cpu().numpy(), h.x.numpy())
+    fl.close()
+
+
+def test_stability_entry_point(ptf, oracle_mod):
+    import torch
+    comp, cond = wl.workload("nc8_1e6", 4000)
+    fl = ptf.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij)
+    P, T, z = _to_dev(cond)
+    stable, tm, K, st = fl.ptflash_stability(P, T, z)
+    torch.cuda.synchronize()
+    s = oracle_mod.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
+    o = oracle_mod.stability(s, cond.P, cond.T, cond.z)
+    tp = oracle_mod.tpd_min(s, cond.P, cond.T, cond.z)
+    graded = np.abs(tp) > 1e-8
+    g = stable.cpu().numpy()
+    assert np.all(g[graded] == (tp[graded] >= 0))
+    assert np.mean(g == o["stable"]) > 0.999
+    fl.close()
+
+
+def test_invalid_arguments(ptf):
+    import ctypes
+    lib = ptf.load()
+    h = ctypes.c_void_p()
+    assert lib.ptflash_create(ctypes.byref(h), 1, 100) == -5
+    assert lib.ptflash_create(ctypes.byref(h), 4, 0) == -1
+    assert lib.ptflash_create(ctypes.byref(h), 4, 100) == 0
+    D = ctypes.POINTER(ctypes.c_double)
+    a = (ctypes.c_double * 16)()
+    Tc = (ctypes.c_double * 4)(300, 400, 500, 600)
+    Pc = (ctypes.c_double * 4)(4, 4, 4, 4)
+    om = (ctypes.c_double * 4)(0.1, 0.1, 0.1, 0.1)
+    k = (ctypes.c_double * 16)(*([0.0] * 16))
+    k[1] = 0.1  # asymmetric
+    assert lib.ptflash_set_components(h, 4, Tc, Pc, om, k) == -1
+    k[4] = 0.1
+    assert lib.ptflash_set_components(h, 4, Tc, Pc, om, k) == 0
+    k[0] = 0.1  # nonzero diagonal
+    assert lib.ptflash_set_components(h, 4, Tc, Pc, om, k) == -1
+    assert lib.ptflash_set_components(h, 5, Tc, Pc, om, k) == -5
+    assert lib.ptflash_flash(h, -1, None, None, None, None, None, None, None, None, None, None, None, None) == -1
+    assert lib.ptflash_flash(h, 10, None, None, None, None, None, None, None, None, None, None, None, None) == -1
+    del a, D
+    assert lib.ptflash_destroy(h) == 0
