@@ -59,7 +59,7 @@ def _lib_handle():
         lib = ctypes.CDLL(_LIB)
         sysargs = [ctypes.c_int, _D, _D, _D, _D]
         lib.oracle_flash_batch.argtypes = sysargs + [ctypes.c_int64, _D, _D, _D, _I, _D, _D, _D, _D, _I, _I, _D,
-                                                     ctypes.c_int]
+                                                     _D, ctypes.c_int]
         lib.oracle_flash_batch.restype = ctypes.c_int
         lib.oracle_tpd_min_batch.argtypes = sysargs + [ctypes.c_int64, _D, _D, _D, _D, ctypes.c_int]
         lib.oracle_tpd_min_batch.restype = ctypes.c_int
@@ -113,8 +113,10 @@ def flash(sysc: System, P, T, z, nthreads: int | None = None):
     """Plain flash (Sec. 2.2.3) of n mixtures; z is component-major [nc, n].
 
     Returns a dict of NumPy arrays: nphase, beta, x, y, K ([nc, n]), status,
-    iters (packed: split SS | split TR << 8 | stab SS << 16 | stab TR << 24)
-    and tm_min (NaN where stability analysis did not run)."""
+    iters (packed: split SS | split TR << 8 | stab SS << 16 | stab TR << 24),
+    tm_min (NaN where stability analysis did not run) and flops: the
+    algorithmic FP64 work summed over the batch per stage (prep+precheck,
+    stability SS, stability TR, split SS, split TR)."""
     P = _f64(P)
     T = _f64(T)
     z = _f64(z)
@@ -123,11 +125,11 @@ def flash(sysc: System, P, T, z, nthreads: int | None = None):
     assert z.shape == (nc, n)
     out = dict(nphase=np.zeros(n, np.int32), beta=np.zeros(n), x=np.zeros((nc, n)), y=np.zeros((nc, n)),
                K=np.zeros((nc, n)), status=np.zeros(n, np.int32), iters=np.zeros(n, np.int32),
-               tm_min=np.zeros(n))
+               tm_min=np.zeros(n), flops=np.zeros(5))
     rc = _lib_handle().oracle_flash_batch(*sysc._args(), n, _p(P), _p(T), _p(z), _pi(out["nphase"]),
                                           _p(out["beta"]), _p(out["x"]), _p(out["y"]), _p(out["K"]),
                                           _pi(out["status"]), _pi(out["iters"]), _p(out["tm_min"]),
-                                          nthreads or default_threads())
+                                          _p(out["flops"]), nthreads or default_threads())
     if rc:
         raise ValueError("oracle_flash_batch failed")
     return out

@@ -95,6 +95,37 @@
 #define PRED_TRUST 1e-12      /* R9: ratio test trusted above this relative size */
 
 /* ------------------------------------------------------------------------ */
+/* Algorithmic FP64 work, counted per stage along the path each mixture      */
+/* takes.  Each primitive is charged the work of the method's own numerics   */
+/* (Halley roots, Newton Rachford-Rice, Cholesky trust-region steps), not of  */
+/* the oracle's slower bracketing: add, multiply = 1 flop, fused multiply-add */
+/* = 2, divide and square root = 8, exp and log = 20 (textbook Newton and     */
+/* polynomial costs).  Stages: 0 prep+precheck, 1 stability SS, 2 stability   */
+/* TR, 3 split SS, 4 split TR.                                               */
+/* ------------------------------------------------------------------------ */
+#define NSTAGE 5
+static _Thread_local double g_flops[NSTAGE];
+static _Thread_local int g_stage;
+#define FLOPS(x) (g_flops[g_stage] += (double)(x))
+#define W_DIV 8.0
+#define W_EXP 20.0
+#define W_LOG 20.0
+/* per-primitive costs */
+static double cost_eos(int nc, int three) {
+    double c = 2.0 * nc * nc + 8.0 * nc     /* mixing sums */
+               + 18.0 + 2 * W_DIV           /* root count: 2 cubic evaluations, sqrt */
+               + 2 * (16.0 + W_DIV)         /* two FP64 Halley steps */
+               + 2 * (W_LOG + W_DIV)        /* ln(Z - B), ln(1 + B/Z) */
+               + 2 * W_DIV + 4.0 + 3.0 * nc;/* ln phi */
+    if (three) c += 10.0 + 2 * W_DIV + 2 * (8.0 + W_DIV) + 2 * (W_LOG + W_DIV) + 8.0; /* deflation, polish, gbar */
+    return c;
+}
+static double cost_jac(int nc) { return 7.0 * nc * (nc + 1) + 30.0 * nc + 8 * W_DIV; }
+static double cost_rr(int nc) { return 4.0 * (nc * (W_DIV + 6.0) + 10.0 + W_DIV) + nc * W_DIV; }
+static double cost_chol(int nc) { return 2.0 * nc * nc * nc / 6.0 + nc * (2 * W_DIV) + 2.0 * nc * nc; }
+static double cost_trsub(int nc) { return 3.0 * cost_chol(nc) + 4.0 * nc * nc; }
+
+/* ------------------------------------------------------------------------ */
 /* Component system and per-mixture EOS constants (Appendix A)              */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -231,6 +262,7 @@ int or_eos(const or_mix* m, const double* c, or_phase* ph) {
     if (!have) return -1;
     double Z = zv;
     if (zl < zv && gbar(zl, A, B) < gbar(zv, A, B)) Z = zl;
+    FLOPS(cost_eos(nc, zl < zv));
     ph->A = A;
     ph->B = B;
     ph->Z = Z;
@@ -251,6 +283,7 @@ int or_eos(const or_mix* m, const double* c, or_phase* ph) {
 /* ------------------------------------------------------------------------ */
 void or_dlnphi_dn(const or_mix* m, const double* c, const or_phase* ph, double* J) {
     int nc = m->nc;
+    FLOPS(cost_jac(nc));
     double A = ph->A, B = ph->B, Z = ph->Z;
     double L = log(1.0 + B / Z);
     double FZ = 3.0 * Z * Z - 2.0 * Z + A - B - B * B;
@@ -295,6 +328,7 @@ int or_rr(int nc, const double* z, const double* K, double* theta) {
     double kmax = K[0], kmin = K[0];
     for (int i = 1; i < nc; i++) { if (K[i] > kmax) kmax = K[i]; if (K[i] < kmin) kmin = K[i]; }
     if (!(kmax > 1.0 && kmin < 1.0)) return -1;
+    FLOPS(cost_rr(nc));
     double lo = 1.0 / (1.0 - kmax), hi = 1.0 / (1.0 - kmin); /* alpha_l < 0 < 1 < alpha_r */
     for (int it = 0; it < 2000; it++) {
         double mid = 0.5 * (lo + hi);
@@ -368,6 +402,7 @@ static double unorm(int n, const double* gt, const double* lam, double eta) {
 }
 
 double or_tr_subproblem(int n, const double* H, const double* g, const double* mdiag, double radius, double* d) {
+    FLOPS(cost_trsub(n));
     double Hs[OR_MAXNC * OR_MAXNC], gs[OR_MAXNC], sc[OR_MAXNC];
     for (int i = 0; i < n; i++) sc[i] = mdiag ? 1.0 / sqrt(mdiag[i]) : 1.0;
     for (int i = 0; i < n; i++) {
@@ -427,6 +462,7 @@ double or_tr_subproblem(int n, const double* H, const double* g, const double* m
 /* Newton step -H^{-1} g through the eigendecomposition; returns 0 if H is
  * positive definite, -1 otherwise (no step). */
 static int newton_step(int n, const double* H, const double* g, double* d) {
+    FLOPS(cost_chol(n) + 2.0 * n * n);
     double lam[OR_MAXNC], V[OR_MAXNC * OR_MAXNC];
     jacobi_eig(n, H, lam, V);
     for (int k = 0; k < n; k++) if (!(lam[k] > 0.0)) return -1;
@@ -480,6 +516,7 @@ typedef struct {
 /* tm (reading R2) and grad-tm/dW = ln W + ln phi(W) - d at a trial lnW. */
 static int stab_eval(const or_mix* m, const double* d, const double* lnW, or_phase* ph, double* gt, double* tm) {
     int nc = m->nc;
+    FLOPS(nc * W_EXP + W_DIV + 6.0 * nc);
     double W[OR_MAXNC], Wt = 0.0, c[OR_MAXNC];
     for (int i = 0; i < nc; i++) { W[i] = exp(lnW[i]); Wt += W[i]; }
     for (int i = 0; i < nc; i++) c[i] = W[i] / Wt;
@@ -499,6 +536,27 @@ static double maxabs(int n, const double* v) {
     return r;
 }
 
+/* Stability trust-region point (Appendix B.1, Eqs. analysis_grad and
+ * analysis_hess with reading R4): gradient g_i = sqrt(W_i) gt_i and Hessian
+ * H_ij = sqrt(W_i W_j) d ln phi_i / d W_j + delta_ij (1 + g_i / beta_i) in
+ * beta = 2 sqrt(W), where g_i / beta_i = gt_i / 2. */
+static int stab_point(const or_mix* m, const double* d, const double* lnW, double* gt, double* tm, double* g,
+                      double* H) {
+    int nc = m->nc;
+    or_phase ph;
+    if (stab_eval(m, d, lnW, &ph, gt, tm)) return -1;
+    double W[OR_MAXNC], Wt = 0.0, c[OR_MAXNC], J[OR_MAXNC * OR_MAXNC];
+    for (int i = 0; i < nc; i++) { W[i] = exp(lnW[i]); Wt += W[i]; }
+    for (int i = 0; i < nc; i++) c[i] = W[i] / Wt;
+    or_dlnphi_dn(m, c, &ph, J);
+    FLOPS(nc * W_DIV + 4.0 * nc * (nc + 1) + 2 * nc);
+    for (int i = 0; i < nc; i++) g[i] = sqrt(W[i]) * gt[i];
+    for (int i = 0; i < nc; i++)
+        for (int j = 0; j < nc; j++)
+            H[i * nc + j] = sqrt(W[i] * W[j]) * J[i * nc + j] / Wt + (i == j ? 1.0 + 0.5 * gt[i] : 0.0);
+    return 0;
+}
+
 /* stop_on_negative = 1 follows the paper (stop at tm < 0); the grading
  * helper passes 0 to converge every trial to its stationary point. */
 void or_stability_trial(const or_mix* m, const double* d, or_trial* tr, int stop_on_negative, int kss, int ktr,
@@ -512,6 +570,7 @@ void or_stability_trial(const or_mix* m, const double* d, or_trial* tr, int stop
      * residual, else the plain update is restored. */
     double lnW_plain[OR_MAXNC], res_prev = INFINITY;
     int dem_pending = 0;
+    g_stage = 1;
     for (int it = 0;; it++) {
         int bad = stab_eval(m, d, tr->lnW, &ph, gt, &tm);
         double res = bad ? INFINITY : maxabs(nc, gt);
@@ -543,24 +602,10 @@ void or_stability_trial(const or_mix* m, const double* d, or_trial* tr, int stop
     /* trust region on beta = 2 sqrt(W), Eqs. tr_sa, analysis_grad,
      * analysis_hess (readings R4, R9) */
     tr->used_tr = 1;
-    double beta[OR_MAXNC], g[OR_MAXNC], H[OR_MAXNC * OR_MAXNC], J[OR_MAXNC * OR_MAXNC];
-    double W[OR_MAXNC], Wt, c[OR_MAXNC];
+    g_stage = 2;
+    double beta[OR_MAXNC], g[OR_MAXNC], H[OR_MAXNC * OR_MAXNC];
     double radius = -1.0;
-    /* evaluate at current point */
-#define STAB_POINT(LNW, PH, GT, TM, G, H_)                                                   \
-    do {                                                                                     \
-        if (stab_eval(m, d, LNW, &PH, GT, &TM)) { tr->nonfinite = 1; tr->tm = NAN; return; } \
-        Wt = 0.0;                                                                            \
-        for (int i = 0; i < nc; i++) { W[i] = exp(LNW[i]); Wt += W[i]; }                     \
-        for (int i = 0; i < nc; i++) c[i] = W[i] / Wt;                                       \
-        or_dlnphi_dn(m, c, &PH, J);                                                          \
-        for (int i = 0; i < nc; i++) G[i] = sqrt(W[i]) * GT[i];                              \
-        for (int i = 0; i < nc; i++)                                                         \
-            for (int j = 0; j < nc; j++)                                                     \
-                H_[i * nc + j] = sqrt(W[i] * W[j]) * J[i * nc + j] / Wt                      \
-                                 + (i == j ? 1.0 + 0.5 * GT[i] : 0.0);                       \
-    } while (0)
-    STAB_POINT(tr->lnW, ph, gt, tm, g, H);
+    if (stab_point(m, d, tr->lnW, gt, &tm, g, H)) { tr->nonfinite = 1; tr->tm = NAN; return; }
     for (int i = 0; i < nc; i++) beta[i] = 2.0 * exp(0.5 * tr->lnW[i]);
     for (int it = 0;; it++) {
         if (stop_on_negative && tm < -EPS_NEG) break;
@@ -573,16 +618,17 @@ void or_stability_trial(const or_mix* m, const double* d, or_trial* tr, int stop
         }
         double pred = or_tr_subproblem(nc, H, g, NULL, radius, step);
         double lnWn[OR_MAXNC], gtn[OR_MAXNC], gn[OR_MAXNC], Hn[OR_MAXNC * OR_MAXNC], tmn;
-        or_phase phn;
         for (int i = 0; i < nc; i++) {
             double b = fabs(beta[i] + step[i]); /* tm(beta) is even in each beta_i */
             lnWn[i] = 2.0 * log(0.5 * b);
         }
-        STAB_POINT(lnWn, phn, gtn, tmn, gn, Hn);
+        FLOPS(nc * (W_LOG + 3.0) + 2.0 * nc * nc);
+        int bad = stab_point(m, d, lnWn, gtn, &tmn, gn, Hn);
         /* R9: below PRED_TRUST the predicted change is under the rounding
-         * of tm itself and the ratio is noise: accept, keep the radius */
+         * of tm itself and the ratio is noise: accept, keep the radius.
+         * A trial point that cannot be evaluated is a rejected step. */
         int trusted = fabs(pred) > PRED_TRUST * (1.0 + fabs(tm));
-        double rho = trusted ? (tmn - tm) / pred : 0.5;
+        double rho = bad ? -1.0 : (trusted ? (tmn - tm) / pred : 0.5);
         if (rho > 0.0) {
             for (int i = 0; i < nc; i++) {
                 tr->lnW[i] = lnWn[i];
@@ -597,7 +643,6 @@ void or_stability_trial(const or_mix* m, const double* d, or_trial* tr, int stop
         else if (rho >= 0.75) radius *= 2.0;
         tr->iters_tr = it + 1;
     }
-#undef STAB_POINT
     tr->tm = tm;
 }
 
@@ -635,6 +680,7 @@ typedef struct {
 
 static int split_eval(const or_mix* m, const double* z, const double* nV, or_splitpt* s) {
     int nc = m->nc;
+    FLOPS(2 * W_DIV + 4.0 * nc + 2.0 * nc * W_LOG + 8.0 * nc + nc * (2 * W_DIV) + 5.0 * nc * (nc + 1) + 2.0 * nc * nc);
     double th = 0.0;
     for (int i = 0; i < nc; i++) th += nV[i];
     s->th = th;
@@ -692,6 +738,7 @@ static void finish_two_phase(int nc, double th, const double* x, const double* y
  * taken by the caller's run (DEM numbering restarts: fresh cap, R11). */
 static void or_split(const or_mix* m, const double* z, double* lnK, or_result* r) {
     int nc = m->nc;
+    g_stage = 3;
     double K[OR_MAXNC], x[OR_MAXNC], y[OR_MAXNC], th = 0.5, dprev[OR_MAXNC] = {0}, dprev2[OR_MAXNC] = {0};
     or_phase pl, pv;
     r->it_split_ss = 0;
@@ -705,6 +752,7 @@ static void or_split(const or_mix* m, const double* z, double* lnK, or_result* r
         if (maxabs(nc, lnK) < TRIVIAL_LNK) fail = 1;
         if (!fail) {
             for (int i = 0; i < nc; i++) K[i] = exp(lnK[i]);
+            FLOPS(nc * W_EXP + 6.0 * nc);
             if (or_rr(nc, z, K, &th)) fail = 1;
         }
         if (!fail) {
@@ -748,6 +796,7 @@ static void or_split(const or_mix* m, const double* z, double* lnK, or_result* r
     /* trust region on G in n^V (Eq. newton_splitter), from the last
      * evaluated SS point (theta, x, y of the cap-th evaluation) */
     r->status |= ST_SPLIT_TR;
+    g_stage = 4;
     double nV[OR_MAXNC];
     if (th > 0.0 && th < 1.0) {
         for (int i = 0; i < nc; i++) nV[i] = th * y[i];
@@ -822,8 +871,10 @@ static void or_split(const or_mix* m, const double* z, double* lnK, or_result* r
 /* ------------------------------------------------------------------------ */
 void or_flash_one(const or_sys* s, double P, double T, const double* z, or_result* r) {
     int nc = s->nc;
+    g_stage = 0;
     or_mix m;
     or_mix_init(s, P, T, &m);
+    FLOPS(nc * (2 * W_DIV + 12.0) + nc * W_LOG + nc * 4.0); /* constants, ln z, Wilson */
     memset(r, 0, sizeof(*r));
     r->tm_min = NAN;
     double lnz[OR_MAXNC], d[OR_MAXNC], lnKw[OR_MAXNC], lnK[OR_MAXNC];
@@ -840,6 +891,7 @@ void or_flash_one(const or_sys* s, double P, double T, const double* z, or_resul
         or_phase pl, pv;
         for (int it = 0; it < NPRECHECK; it++) {
             for (int i = 0; i < nc; i++) K[i] = exp(lnK[i]);
+            FLOPS(nc * W_EXP + 6.0 * nc);
             if (or_rr(nc, z, K, &th) || !(th > 0.0 && th < 1.0)) { route_stab = 1; break; }
             xy_from(nc, z, K, th, x, y);
             if (or_eos(&m, x, &pl) || or_eos(&m, y, &pv)) { route_stab = 1; break; }
@@ -848,6 +900,7 @@ void or_flash_one(const or_sys* s, double P, double T, const double* z, or_resul
         if (!route_stab) {
             /* Eq. tpd on the current phases; Delta G by reading R3 */
             double tx = 0.0, ty = 0.0;
+            FLOPS(2.0 * nc * (W_LOG + 4.0) + 5.0);
             for (int i = 0; i < nc; i++) {
                 tx += x[i] * (log(x[i]) + pl.lnphi[i] - d[i]);
                 ty += y[i] * (log(y[i]) + pv.lnphi[i] - d[i]);
@@ -926,11 +979,15 @@ static void sys_from(int nc, const double* Tc, const double* Pc, const double* o
 int oracle_flash_batch(int nc, const double* Tc, const double* Pc, const double* om, const double* kij,
                        int64_t n, const double* P, const double* T, const double* z,
                        int32_t* nphase, double* beta, double* x, double* y, double* K,
-                       int32_t* status, int32_t* iters, double* tm_min, int nthreads) {
+                       int32_t* status, int32_t* iters, double* tm_min, double* flops, int nthreads) {
     if (nc < 2 || nc > OR_MAXNC) return -1;
     or_sys s;
     sys_from(nc, Tc, Pc, om, kij, &s);
-#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+    double tot[NSTAGE] = {0};
+#pragma omp parallel num_threads(nthreads)
+    {
+    for (int q = 0; q < NSTAGE; q++) g_flops[q] = 0.0;
+#pragma omp for schedule(dynamic, 16)
     for (int64_t k = 0; k < n; k++) {
         double zz[OR_MAXNC];
         for (int i = 0; i < nc; i++) zz[i] = z[(int64_t)i * n + k];
@@ -947,6 +1004,11 @@ int oracle_flash_batch(int nc, const double* Tc, const double* Pc, const double*
         if (iters) iters[k] = (r.it_split_ss & 0xff) | ((r.it_split_tr & 0xff) << 8) | ((r.it_stab_ss & 0xff) << 16) | ((r.it_stab_tr & 0xff) << 24);
         if (tm_min) tm_min[k] = r.tm_min;
     }
+#pragma omp critical
+    for (int q = 0; q < NSTAGE; q++) tot[q] += g_flops[q];
+    }
+    if (flops)
+        for (int q = 0; q < NSTAGE; q++) flops[q] = tot[q];
     return 0;
 }
 
