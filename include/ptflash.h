@@ -146,6 +146,31 @@ int ptflash_last_counts(ptflash_ctx* ctx, int64_t* counts);
 int ptflash_set_profiling(ptflash_ctx* ctx, int enable);
 int ptflash_last_stage_ms(ptflash_ctx* ctx, double* ms, int count);
 
+/*
+ * ptflash_flash without any device allocation.  The paper has no
+ * counterpart: this serves callers that cannot allocate device memory once
+ * running -- a simulator time-step loop that budgeted all GPU memory at
+ * start-up, a host application whose own allocator owns the device heap, or
+ * code that cannot afford the device-wide synchronisation cudaMalloc /
+ * cudaFree may imply.  It takes the component data as HOST arrays (as
+ * ptflash_set_components) and every batch array as a DEVICE array (as
+ * ptflash_flash); no context is needed.  Its scratch is one file-scope
+ * device array of 64 MiB that every GPU which loads this library holds until
+ * the process exits; it calls no cudaMalloc, cudaFree or allocating library
+ * routine.  n may not exceed ptflash_noalloc_max_mixtures(nc) (e.g. 118,000
+ * mixtures at nc = 8): larger n returns PTF_ERR_INVALID_ARG.
+ * The first call on a device (with that device current) looks up the
+ * scratch's device address; make that first call before any stream capture.
+ * Every call shares the one scratch array, which keeps the previous call's
+ * contents (the call clears what must start at zero): calls that overlap on
+ * the GPU -- from different streams or threads -- race and must not be made.
+ */
+int64_t ptflash_noalloc_max_mixtures(int nc);
+int ptflash_flash_noalloc(int nc, const double* Tc, const double* Pc, const double* omega, const double* kij,
+                          int64_t n, const double* P, const double* T, const double* z, int32_t* nphase,
+                          double* beta, double* x, double* y, double* K, int32_t* status, int32_t* iters,
+                          void* stream);
+
 /* Human-readable name of an error code. */
 const char* ptflash_strerror(int code);
 

@@ -13,7 +13,7 @@ def _declared():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        names |= set(re.findall(r"\b(?:int|const char\s*\*)\s+(ptflash_\w+)\s*\(", src))
+        names |= set(re.findall(r"\b(?:int|int64_t|const char\s*\*)\s+(ptflash_\w+)\s*\(", src))
     return names
 
 
