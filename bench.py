@@ -39,7 +39,7 @@ FP64_FMA_PER_CLK_PER_SM = 2  # GB300 FP64 units (recipe: 1.25 TFLOP/s at 2.07 GH
 TOL = 1e-8
 LIB_STAGES = ("prep_precheck", "stab_ss", "stab_tr", "stab_decide", "split_ss", "split_tr")
 ORACLE_STAGE = {"prep_precheck": 0, "stab_ss": 1, "stab_tr": 2, "split_ss": 3, "split_tr": 4}
-KERNELS_PER_STEP = 7  # 6 stage kernels + the counter fold
+KERNELS_PER_STEP = 8  # 7 stage kernels + the counter fold
 
 
 def dist_env():
@@ -166,7 +166,8 @@ def ours_arm(args, ws, rank, local):
     build.build()
     w = dict(wl.WORKLOADS[WORKLOAD])
     comp = wl.pseudo_components(w["nc"], w["comp_seed"])
-    cond = wl.conditions(w["nc"], w["n"], w["cond_seed"] + 1000 * rank, w["T_range"], w["P_range"], w["alpha"])
+    n_mix = args.n or w["n"]
+    cond = wl.conditions(w["nc"], n_mix, w["cond_seed"] + 1000 * rank, w["T_range"], w["P_range"], w["alpha"])
     n, nc = cond.n, comp.nc
     fl = ptflash.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=n)
     P = torch.tensor(cond.P, device=dev)
@@ -244,14 +245,18 @@ def ours_arm(args, ws, rank, local):
 
     # CPU baseline (the oracle as it stands) on a bounded sample, which also
     # gives the oracle-matching fraction and the algorithmic FP64 work
-    rng = np.random.default_rng(11)
+    # (--cpu-sample 0 skips it: diagnostic runs only, no valid value)
     sample = min(n, args.cpu_sample)
-    idx = np.sort(rng.choice(n, sample, replace=False))
-    o, cpu_dt, s = run_oracle_sample(comp, cond, idx)
-    import oracle as _or
-    cores = _or.default_threads()
-    frac = match_fraction(s, comp, cond, idx, o, g)
-    flops_per_flash = o["flops"] / sample  # by oracle stage
+    if sample > 0:
+        rng = np.random.default_rng(11)
+        idx = np.sort(rng.choice(n, sample, replace=False))
+        o, cpu_dt, s = run_oracle_sample(comp, cond, idx)
+        import oracle as _or
+        cores = _or.default_threads()
+        frac = match_fraction(s, comp, cond, idx, o, g)
+        flops_per_flash = o["flops"] / sample  # by oracle stage
+    else:
+        cpu_dt, cores, frac, flops_per_flash = float("nan"), 0, float("nan"), np.full(5, np.nan)
 
     mean_stage = {k: float(np.mean([d[k] for d in stage_ms])) for k in LIB_STAGES}
     dom = max(mean_stage, key=mean_stage.get)
@@ -298,6 +303,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-sample", type=int, default=100_000)
     ap.add_argument("--ref-sample", type=int, default=20_000)
+    ap.add_argument("--n", type=int, default=0, help="mixtures per rank (default: the workload's 1e6)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

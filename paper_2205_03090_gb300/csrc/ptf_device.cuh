@@ -127,10 +127,12 @@ __device__ __forceinline__ Root cubic_select(double A, double B) {
             float fp = fmaf(fmaf(3.0f, zf, -2.0f), zf, r1f);
             float fpp = fmaf(6.0f, zf, -2.0f);
             float zn = zf - 2.0f * f * fp / (2.0f * fp * fp - f * fpp);
+            if (fabsf(zn - zf) <= 1e-6f * zf) {  // converged: accept before any bracket test
+                zf = zn;
+                break;
+            }
             if (!(zn > lof && zn < hif)) zn = 0.5f * (lof + hif);
-            bool done = fabsf(zn - zf) <= 1e-6f * zf;
             zf = zn;
-            if (done) break;
         }
     }
     // FP64 bracketed Halley from the seed
@@ -143,14 +145,16 @@ __device__ __forceinline__ Root cubic_select(double A, double B) {
         double fp = cub_df(z0, r1);
         double fpp = fma(6.0, z0, -2.0);
         double zn = z0 - 2.0 * f * fp / (2.0 * fp * fp - f * fpp);
+        if (fabs(zn - z0) <= 1e-8 * fabs(zn)) {  // converged (Appendix A criterion)
+            z0 = zn;
+            break;
+        }
         if (!(zn > lo && zn < hi)) {
-            z0 = 0.5 * (lo + hi);  // bisection
+            z0 = 0.5 * (lo + hi);  // bisection when the step leaves the bracket
             if (hi - lo <= 1e-15 * z0) break;
             continue;
         }
-        bool done = fabs(zn - z0) <= 1e-8 * fabs(zn);
         z0 = zn;
-        if (done) break;
     }
     double zl = z0, zv = z0;
     if (three) {
@@ -267,7 +271,8 @@ __device__ __forceinline__ void dlnphi_dn(const Comp<NC>& cp, const Mix<NC>& mx,
 // ---------------------------------------------------------------------------
 // Rachford-Rice (Eq. RR) on the Leibovici-Neoschil window (Appendix C):
 // Newton on h = (theta - a_l)(a_r - theta) f_RR inside a shrinking bracket,
-// bisection when Newton leaves it; run to full precision.  Returns false if
+// bisection when Newton leaves it; stops after a Newton step below 1e-8
+// (quadratic convergence leaves an error of order 1e-16).  Returns false if
 // K does not bracket 1.  On success t[i] = 1 / (1 + (K_i - 1) theta).
 // ---------------------------------------------------------------------------
 template <int NC>
@@ -301,10 +306,15 @@ __device__ __forceinline__ bool rachford_rice(const double* z, const double* K, 
         double h = g1 * g2 * f;
         double hp = (g2 - g1) * f + g1 * g2 * fp;
         double tn = th - h / hp;
-        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
-        double step = fabs(tn - th);
+        // stop once the Newton step is below 1e-8 (Appendix C); the step just
+        // taken leaves an error of order its square
+        if (fabs(tn - th) <= 1e-8 * fmax(1.0, fabs(th))) {
+            th = tn;
+            break;
+        }
+        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);  // bisection
         th = tn;
-        if (step <= 1e-15 * fmax(1.0, fabs(th)) || lo >= hi) break;
+        if (lo >= hi) break;
     }
 #pragma unroll
     for (int i = 0; i < NC; i++) t[i] = 1.0 / fma(km1[i], th, 1.0);

@@ -41,7 +41,10 @@ struct IO {
     int32_t* iters;  // packed: split SS | split TR << 8 | stab SS << 16 | stab TR << 24 (may be null)
 };
 
+// ws.cnt slots: append counters of the queues, and read heads of the
+// persistent (refill) kernels
 enum { Q_STAB = 0, Q_SPLIT = 1, Q_STAB_TR = 2, Q_SPLIT_TR = 3 };
+enum { H_PRE = 8, H_STAB = 9, H_STAB_TR = 10, H_SPLIT = 11, H_SPLIT_TR = 12 };
 
 // Warp-aggregated append: every lane of the warp must call it (full mask).
 __device__ __forceinline__ void warp_append(int32_t* cnt, int32_t* queue, bool pred, int32_t value) {
@@ -51,6 +54,24 @@ __device__ __forceinline__ void warp_append(int32_t* cnt, int32_t* queue, bool p
     if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (pred) queue[base + __popc(m & ((1u << lane) - 1u))] = value;
+}
+
+// Refill for persistent kernels: the lanes that need work (need = true) take
+// the next positions of a queue whose read head is *head; returns this lane's
+// position, or -1 if it needs none or the queue is exhausted.  Every lane of
+// the warp must call it.  `drained` (warp-uniform) stops further atomics.
+__device__ __forceinline__ int64_t warp_fetch(int32_t* head, bool need, int64_t len, bool& drained) {
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    const int lane = threadIdx.x & 31;
+    int64_t base = len;
+    if (m && !drained) {
+        int b = 0;
+        if (lane == 0) b = atomicAdd(head, __popc(m));
+        base = __shfl_sync(0xffffffffu, b, 0);
+        if (base + __popc(m) >= len) drained = true;  // this fetch reached the end
+    }
+    const int64_t pos = base + __popc(m & ((1u << lane) - 1u));
+    return (need && pos < len) ? pos : -1;
 }
 
 // Loop over items in whole-warp rounds so that queue appends see a converged
@@ -101,108 +122,146 @@ __device__ __forceinline__ void write_two(const IO& io, int64_t m, double th, co
 }
 
 // ---------------------------------------------------------------------------
-// prep + precheck (Sec. 2.2.3): three SS iterations from Wilson K.
+// prep (Appendix A): per-mixture constants, ln z, d = ln z + ln phi(z).
+// Uniform work, one thread per mixture.  Non-finite inputs get their final
+// outputs here; the stability-only pipeline enqueues every other mixture.
 // ---------------------------------------------------------------------------
-// Returns the route of mixture m: 0 done, 1 stability queue, 2 split queue.
+// Returns 0 done (non-finite), 1 to the stability queue, 2 to the precheck.
 template <int NC, bool PRECHECK>
 __device__ __forceinline__ int prep_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t m) {
     const int64_t n = ws.n;
-    bool to_stab = false, to_split = false;
-    {
-        {
-            const double P = io.P[m], T = io.T[m];
-            double z[NC], lnz[NC], d[NC];
+    const double P = io.P[m], T = io.T[m];
+    double z[NC];
 #pragma unroll
-            for (int i = 0; i < NC; i++) z[i] = io.z[i * io.ld + m];
-            Mix<NC> mx;
-            mix_init<NC>(cp, P, T, mx);
-            Phase<NC> pz;
-            eos<NC>(cp, mx, z, pz);
-            bool finite = true;
+    for (int i = 0; i < NC; i++) z[i] = io.z[i * io.ld + m];
+    Mix<NC> mx;
+    mix_init<NC>(cp, P, T, mx);
+    Phase<NC> pz;
+    eos<NC>(cp, mx, z, pz);
+    bool finite = true;
 #pragma unroll
-            for (int i = 0; i < NC; i++) {
-                lnz[i] = log(z[i]);
-                d[i] = lnz[i] + pz.lnphi[i];
-                finite = finite && isfinite(d[i]);
-                ws.sA[i * n + m] = mx.sA[i];
-                ws.B[i * n + m] = mx.B[i];
-                ws.lnz[i * n + m] = lnz[i];
-                ws.d[i * n + m] = d[i];
-            }
-            int32_t st = 0;
-            if (!finite || !(P > 0.0 && T > 0.0)) {
-                st = ST_NONFINITE;
-                if (PRECHECK) {
-                    write_single<NC>(io, m, z);
-                } else {  // stability-only outputs: stable, tm = NaN, K = 1
-                    io.nphase[m] = 1;
-                    io.beta[m] = NAN;
-#pragma unroll
-                    for (int i = 0; i < NC; i++) io.K[i * io.ld + m] = 1.0;
-                }
-            } else if (!PRECHECK) {
-                to_stab = true;
-                st = ST_STAB_RUN;
-            } else {
-                double lnK[NC], K[NC], t[NC], x[NC], y[NC];
-                wilson<NC>(cp, P, T, lnK);
-                Phase<NC> pl, pv;
-                double th = 0.5;
-                bool stab = false;
-#pragma unroll 1
-                for (int it = 0; it < kPrecheck; it++) {
-#pragma unroll
-                    for (int i = 0; i < NC; i++) K[i] = exp(lnK[i]);
-                    if (!rachford_rice<NC>(z, K, th, t) || !(th > 0.0 && th < 1.0)) {
-                        stab = true;
-                        break;
-                    }
-#pragma unroll
-                    for (int i = 0; i < NC; i++) {
-                        x[i] = z[i] * t[i];
-                        y[i] = K[i] * x[i];
-                    }
-                    eos<NC>(cp, mx, x, pl);
-                    eos<NC>(cp, mx, y, pv);
-#pragma unroll
-                    for (int i = 0; i < NC; i++) lnK[i] -= lnK[i] + pv.lnphi[i] - pl.lnphi[i];
-                }
-                if (!stab) {
-                    // Eq. tpd for the current phases; Delta G = (1-theta) tpd(x) + theta tpd(y)
-                    double tx = 0.0, ty = 0.0;
-#pragma unroll
-                    for (int i = 0; i < NC; i++) {
-                        double lx = log(x[i]);
-                        double ly = log(y[i]);
-                        tx = fma(x[i], lx + pl.lnphi[i] - d[i], tx);
-                        ty = fma(y[i], ly + pv.lnphi[i] - d[i], ty);
-                    }
-                    double dG = (1.0 - th) * tx + th * ty;
-                    stab = !(tx < -kEpsNeg || ty < -kEpsNeg || dG < -kEpsNeg);
-                }
-                if (stab) {
-                    to_stab = true;
-                    st = ST_STAB_RUN;
-                } else {
-                    to_split = true;
-                    st = ST_PRECHECK_UNSTABLE;
-#pragma unroll
-                    for (int i = 0; i < NC; i++) ws.lnK[i * n + m] = lnK[i];
-                }
-            }
-            io.status[m] = st;
-            if (io.iters) io.iters[m] = 0;
-        }
+    for (int i = 0; i < NC; i++) {
+        const double lz = log(z[i]);
+        const double d = lz + pz.lnphi[i];
+        finite = finite && isfinite(d);
+        ws.sA[i * n + m] = mx.sA[i];
+        ws.B[i * n + m] = mx.B[i];
+        ws.lnz[i * n + m] = lz;
+        ws.d[i * n + m] = d;
     }
-    return to_stab ? 1 : (to_split ? 2 : 0);
+    if (io.iters) io.iters[m] = 0;
+    if (!finite || !(P > 0.0 && T > 0.0)) {
+        io.status[m] = ST_NONFINITE;
+        if (PRECHECK) {
+            write_single<NC>(io, m, z);
+        } else {  // stability-only outputs: stable, tm = NaN, K = 1
+            io.nphase[m] = 1;
+            io.beta[m] = NAN;
+#pragma unroll
+            for (int i = 0; i < NC; i++) io.K[i * io.ld + m] = 1.0;
+        }
+        return 0;
+    }
+    if (!PRECHECK) {
+        io.status[m] = ST_STAB_RUN;
+        return 1;
+    }
+    io.status[m] = 0;
+    return 2;
 }
 
 template <int NC, bool PRECHECK>
-__global__ void __launch_bounds__(128) k_prep_precheck(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+__global__ void __launch_bounds__(128) k_prep(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
     PTF_WARP_ROUNDS(ws.n, m, valid) {
         const int route = valid ? prep_item<NC, PRECHECK>(cp, ws, io, m) : 0;
         warp_append(ws.cnt + Q_STAB, ws.q_stab, route == 1, (int32_t)m);
-        warp_append(ws.cnt + Q_SPLIT, ws.q_split, route == 2, (int32_t)m);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// precheck (Sec. 2.2.3): three split-SS evaluations from Wilson K, then the
+// tpd(x), tpd(y), Delta G tests.  One step = one evaluation of one mixture.
+// ---------------------------------------------------------------------------
+template <int NC>
+struct PrecheckSS {
+    int64_t m;
+    Mix<NC> mx;
+    double z[NC], lnK[NC], th;
+    int it;
+
+    __device__ __forceinline__ void begin(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t mm) {
+        m = mm;
+        load_mix<NC>(ws, m, mx);
+#pragma unroll
+        for (int i = 0; i < NC; i++) z[i] = io.z[i * io.ld + m];
+        wilson<NC>(cp, io.P[m], io.T[m], lnK);
+        th = 0.5;
+        it = 0;
+    }
+
+    // 0 continue, 1 to the stability queue, 2 to the split queue
+    __device__ __forceinline__ int step(const Comp<NC>& cp, const WS& ws, const IO& io) {
+        const int64_t n = ws.n;
+        double K[NC], t[NC], x[NC], y[NC];
+        Phase<NC> pl, pv;
+#pragma unroll
+        for (int i = 0; i < NC; i++) K[i] = exp(lnK[i]);
+        if (!rachford_rice<NC>(z, K, th, t) || !(th > 0.0 && th < 1.0)) {
+            io.status[m] = ST_STAB_RUN;
+            return 1;
+        }
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            x[i] = z[i] * t[i];
+            y[i] = K[i] * x[i];
+        }
+        eos<NC>(cp, mx, x, pl);
+        eos<NC>(cp, mx, y, pv);
+#pragma unroll
+        for (int i = 0; i < NC; i++) lnK[i] -= lnK[i] + pv.lnphi[i] - pl.lnphi[i];
+        if (++it < kPrecheck) return 0;
+        // Eq. tpd for the current phases; Delta G = (1-theta) tpd(x) + theta tpd(y)
+        double tx = 0.0, ty = 0.0;
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            const double d = ws.d[i * n + m];
+            tx = fma(x[i], log(x[i]) + pl.lnphi[i] - d, tx);
+            ty = fma(y[i], log(y[i]) + pv.lnphi[i] - d, ty);
+        }
+        const double dG = (1.0 - th) * tx + th * ty;
+        if (!(tx < -kEpsNeg || ty < -kEpsNeg || dG < -kEpsNeg)) {
+            io.status[m] = ST_STAB_RUN;
+            return 1;
+        }
+        io.status[m] = ST_PRECHECK_UNSTABLE;
+#pragma unroll
+        for (int i = 0; i < NC; i++) ws.lnK[i * n + m] = lnK[i];
+        return 2;
+    }
+};
+
+// Persistent kernel: lanes whose mixture finished take the next one, so the
+// warp keeps all lanes busy until the batch is exhausted.
+template <int NC>
+__global__ void __launch_bounds__(128) k_precheck(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+    const int64_t len = ws.n;
+    PrecheckSS<NC> s;
+    bool have = false, drained = false;
+    for (;;) {
+        const int64_t pos = warp_fetch(ws.cnt + H_PRE, !have, len, drained);
+        if (pos >= 0) {
+            if (io.status[pos] & ST_NONFINITE) {
+                // already final; this lane fetches again next round
+            } else {
+                s.begin(cp, ws, io, pos);
+                have = true;
+            }
+        }
+        if (!__any_sync(0xffffffffu, have) && drained) break;
+        const int r = have ? s.step(cp, ws, io) : 0;
+        warp_append(ws.cnt + Q_STAB, ws.q_stab, r == 1, (int32_t)s.m);
+        warp_append(ws.cnt + Q_SPLIT, ws.q_split, r == 2, (int32_t)s.m);
+        if (r) have = false;
     }
 }
 
@@ -235,90 +294,115 @@ __device__ __forceinline__ bool stab_eval(const Comp<NC>& cp, const Mix<NC>& mx,
 
 // ---------------------------------------------------------------------------
 // Stability SS (Sec. 2.2.1, Eq. ss_analyser) with DEM; item = 2 q + trial.
+// One step = one evaluation of one trial.
 // ---------------------------------------------------------------------------
-// Returns true if the trial needs the trust region.
 template <int NC>
-__device__ __forceinline__ bool stab_ss_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t item) {
-    const int64_t n = ws.n;
-    bool need_tr = false;
-    {
-        {
-            const int64_t m = ws.q_stab[item >> 1];
-            const int t = (int)(item & 1);
-            Mix<NC> mx;
-            load_mix<NC>(ws, m, mx);
-            double d[NC], lnW[NC], lnKw[NC];
-            wilson<NC>(cp, io.P[m], io.T[m], lnKw);
+struct StabSS {
+    int64_t m, item;
+    Mix<NC> mx;
+    double d[NC], lnW[NC], dp[NC], dp2[NC], dem_f, res_prev, tm;
+    int t, it, iters;
+    bool dem_pending;
+
+    __device__ __forceinline__ void begin(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t it_) {
+        const int64_t n = ws.n;
+        item = it_;
+        m = ws.q_stab[item >> 1];
+        t = (int)(item & 1);
+        load_mix<NC>(ws, m, mx);
+        double lnKw[NC];
+        wilson<NC>(cp, io.P[m], io.T[m], lnKw);
 #pragma unroll
-            for (int i = 0; i < NC; i++) {
-                d[i] = ws.d[i * n + m];
-                double lz = ws.lnz[i * n + m];
-                lnW[i] = t == 0 ? lz + lnKw[i] : lz - lnKw[i];  // W = K z (vapour-like), z / K (liquid-like)
-            }
-            double W[NC], c[NC], gt[NC], Wt, tm = 0.0, res_prev = INFINITY;
-            double dp[NC], dp2[NC], lnWp[NC];
-#pragma unroll
-            for (int i = 0; i < NC; i++) dp[i] = dp2[i] = 0.0;
-            Phase<NC> ph;
-            int iters = 0, nonfinite = 0;
-            bool dem_pending = false, done = false;
-#pragma unroll 1
-            for (int it = 0;; it++) {
-                bool bad = !stab_eval<NC>(cp, mx, d, lnW, W, Wt, c, ph, gt, tm);
-                double res = bad ? INFINITY : maxabs<NC>(gt);
-                if (dem_pending && (bad || !(res < res_prev))) {
-                    dem_pending = false;
-#pragma unroll
-                    for (int i = 0; i < NC; i++) lnW[i] = lnWp[i];
-                    continue;
-                }
-                dem_pending = false;
-                if (bad) { nonfinite = 1; done = true; tm = NAN; break; }
-                if (tm < -kEpsNeg) { done = true; break; }
-                if (res < kTolStab) { done = true; break; }
-                if (it >= kSSStab) break;
-                double dk[NC];
-#pragma unroll
-                for (int i = 0; i < NC; i++) {
-                    dk[i] = -gt[i];
-                    lnW[i] += dk[i];
-                }
-                int s = iters + 1;
-                if (s % 5 == 0) {
-                    double f = dem_factor<NC>(dk, dp, dp2);
-                    if (f > 0.0) {
-#pragma unroll
-                        for (int i = 0; i < NC; i++) {
-                            lnWp[i] = lnW[i];
-                            lnW[i] += dk[i] * f;
-                        }
-                        dem_pending = true;
-                        res_prev = res;
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < NC; i++) {
-                    dp2[i] = dp[i];
-                    dp[i] = dk[i];
-                }
-                iters = s;
-            }
-#pragma unroll
-            for (int i = 0; i < NC; i++) ws.lnW[(t * NC + i) * n + m] = lnW[i];
-            ws.tm[t * n + m] = tm;
-            ws.tflag[t * n + m] = iters | (done ? 0 : (1 << 16)) | (nonfinite << 18);
-            need_tr = !done;
+        for (int i = 0; i < NC; i++) {
+            d[i] = ws.d[i * n + m];
+            const double lz = ws.lnz[i * n + m];
+            lnW[i] = t == 0 ? lz + lnKw[i] : lz - lnKw[i];  // W = K z (vapour-like), z / K (liquid-like)
+            dp[i] = dp2[i] = 0.0;
         }
+        res_prev = INFINITY;
+        dem_f = 0.0;
+        tm = 0.0;
+        it = iters = 0;
+        dem_pending = false;
     }
-    return need_tr;
-}
+
+    __device__ __forceinline__ void store(const WS& ws, int flags) {
+        const int64_t n = ws.n;
+#pragma unroll
+        for (int i = 0; i < NC; i++) ws.lnW[(t * NC + i) * n + m] = lnW[i];
+        ws.tm[t * n + m] = tm;
+        ws.tflag[t * n + m] = iters | flags;
+    }
+
+    // 0 continue, 1 done, 2 needs the trust region
+    __device__ __forceinline__ int step(const Comp<NC>& cp, const WS& ws, const IO& io) {
+        double W[NC], c[NC], gt[NC], Wt;
+        Phase<NC> ph;
+        const bool bad = !stab_eval<NC>(cp, mx, d, lnW, W, Wt, c, ph, gt, tm);
+        const double res = bad ? INFINITY : maxabs<NC>(gt);
+        const int this_it = it++;
+        if (dem_pending && (bad || !(res < res_prev))) {  // undo the accelerated update
+            dem_pending = false;
+#pragma unroll
+            for (int i = 0; i < NC; i++) lnW[i] -= dp[i] * dem_f;
+            return 0;  // the next step re-evaluates the plain update
+        }
+        dem_pending = false;
+        if (bad) {
+            tm = NAN;
+            store(ws, 1 << 18);
+            return 1;
+        }
+        if (tm < -kEpsNeg || res < kTolStab) {
+            store(ws, 0);
+            return 1;
+        }
+        if (this_it >= kSSStab) {
+            store(ws, 1 << 16);
+            return 2;
+        }
+        double dk[NC];
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            dk[i] = -gt[i];
+            lnW[i] += dk[i];
+        }
+        const int s = iters + 1;
+        if (s % 5 == 0) {
+            const double f = dem_factor<NC>(dk, dp, dp2);
+            if (f > 0.0) {
+#pragma unroll
+                for (int i = 0; i < NC; i++) lnW[i] += dk[i] * f;
+                dem_f = f;
+                dem_pending = true;
+                res_prev = res;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            dp2[i] = dp[i];
+            dp[i] = dk[i];
+        }
+        iters = s;
+        return 0;
+    }
+};
 
 template <int NC>
 __global__ void __launch_bounds__(128) k_stab_ss(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
     const int64_t len = 2 * (int64_t)(*(volatile int32_t*)(ws.cnt + Q_STAB));
-    PTF_WARP_ROUNDS(len, item, valid) {
-        const bool need_tr = valid ? stab_ss_item<NC>(cp, ws, io, item) : false;
-        warp_append(ws.cnt + Q_STAB_TR, ws.q_stab_tr, need_tr, (int32_t)item);
+    StabSS<NC> s;
+    bool have = false, drained = false;
+    for (;;) {
+        const int64_t pos = warp_fetch(ws.cnt + H_STAB, !have, len, drained);
+        if (pos >= 0) {
+            s.begin(cp, ws, io, pos);
+            have = true;
+        }
+        if (!__any_sync(0xffffffffu, have)) break;
+        const int r = have ? s.step(cp, ws, io) : 0;
+        warp_append(ws.cnt + Q_STAB_TR, ws.q_stab_tr, r == 2, (int32_t)s.item);
+        if (r) have = false;
     }
 }
 
@@ -486,122 +570,144 @@ __global__ void __launch_bounds__(128) k_stab_decide(const __grid_constant__ Com
 
 // ---------------------------------------------------------------------------
 // Phase-split SS (Sec. 2.2.2) with DEM, convergence at the fugacity residual.
+// One step = one evaluation (Rachford-Rice, both phases) of one mixture.
 // ---------------------------------------------------------------------------
-// Returns true if the split needs the trust region.
 template <int NC>
-__device__ __forceinline__ bool split_ss_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t m) {
-    const int64_t n = ws.n;
-    bool need_tr = false;
-    {
-        {
-            Mix<NC> mx;
-            load_mix<NC>(ws, m, mx);
-            double z[NC], lnK[NC], K[NC], t[NC], x[NC], y[NC], gt[NC];
-            double dp[NC], dp2[NC], lnKp[NC];
+struct SplitSS {
+    int64_t m;
+    Mix<NC> mx;
+    double z[NC], lnK[NC], dp[NC], dp2[NC], dem_f, res_prev, th;
+    int it, iters;
+    bool dem_pending;
+
+    __device__ __forceinline__ void begin(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t mm) {
+        const int64_t n = ws.n;
+        m = mm;
+        load_mix<NC>(ws, m, mx);
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            z[i] = io.z[i * io.ld + m];
+            lnK[i] = ws.lnK[i * n + m];
+            dp[i] = dp2[i] = 0.0;
+        }
+        th = 0.5;
+        res_prev = INFINITY;
+        dem_f = 0.0;
+        it = iters = 0;
+        dem_pending = false;
+    }
+
+    __device__ __forceinline__ void finish(const IO& io, int32_t add_status) {
+        io.status[m] |= add_status;
+        if (io.iters) io.iters[m] = (io.iters[m] & ~0xff) | (iters & 0xff);
+    }
+
+    // 0 continue, 1 done, 2 needs the trust region
+    __device__ __forceinline__ int step(const Comp<NC>& cp, const WS& ws, const IO& io) {
+        const int64_t n = ws.n;
+        double K[NC], t[NC], x[NC], y[NC], gt[NC];
+        Phase<NC> pl, pv;
+        int fail = 0;  // 1 collapse (trivial K / no Rachford-Rice root), 2 non-finite
+        double res = INFINITY;
+        if (maxabs<NC>(lnK) < kTrivialLnK) fail = 1;
+        if (!fail) {
+#pragma unroll
+            for (int i = 0; i < NC; i++) K[i] = exp(lnK[i]);
+            if (!rachford_rice<NC>(z, K, th, t)) fail = 1;
+        }
+        if (!fail) {
 #pragma unroll
             for (int i = 0; i < NC; i++) {
-                z[i] = io.z[i * io.ld + m];
-                lnK[i] = ws.lnK[i * n + m];
-                dp[i] = dp2[i] = 0.0;
+                x[i] = z[i] * t[i];
+                y[i] = K[i] * x[i];
             }
-            int32_t st = io.status[m];
-            Phase<NC> pl, pv;
-            double th = 0.5, res_prev = INFINITY;
-            int iters = 0;
-            bool dem_pending = false;
-            int outcome = 0;  // 0 -> TR, 1 converged, 2 collapse, 3 nonfinite
-#pragma unroll 1
-            for (int it = 0;; it++) {
-                int fail = 0;
-                double res = INFINITY;
-                if (maxabs<NC>(lnK) < kTrivialLnK) fail = 1;
-                if (!fail) {
+            eos<NC>(cp, mx, x, pl);
+            eos<NC>(cp, mx, y, pv);
 #pragma unroll
-                    for (int i = 0; i < NC; i++) K[i] = exp(lnK[i]);
-                    if (!rachford_rice<NC>(z, K, th, t)) fail = 1;
-                }
-                if (!fail) {
-#pragma unroll
-                    for (int i = 0; i < NC; i++) {
-                        x[i] = z[i] * t[i];
-                        y[i] = K[i] * x[i];
-                    }
-                    eos<NC>(cp, mx, x, pl);
-                    eos<NC>(cp, mx, y, pv);
-#pragma unroll
-                    for (int i = 0; i < NC; i++) gt[i] = lnK[i] + pv.lnphi[i] - pl.lnphi[i];
-                    res = maxabs<NC>(gt);
-                    if (!(res < INFINITY)) fail = 2;
-                }
-                if (dem_pending && (fail || !(res < res_prev))) {
-                    dem_pending = false;
-#pragma unroll
-                    for (int i = 0; i < NC; i++) lnK[i] = lnKp[i];
-                    continue;
-                }
-                dem_pending = false;
-                if (fail == 1) { outcome = 2; break; }
-                if (fail == 2) { outcome = 3; break; }
-                if (res <= kTolFug) { outcome = (th > 0.0 && th < 1.0) ? 1 : 2; break; }
-                if (it >= kSSSplit) break;
-                double dk[NC];
-#pragma unroll
-                for (int i = 0; i < NC; i++) {
-                    dk[i] = -gt[i];
-                    lnK[i] += dk[i];
-                }
-                int s = iters + 1;
-                if (s % 5 == 0) {
-                    double f = dem_factor<NC>(dk, dp, dp2);
-                    if (f > 0.0) {
-#pragma unroll
-                        for (int i = 0; i < NC; i++) {
-                            lnKp[i] = lnK[i];
-                            lnK[i] += dk[i] * f;
-                        }
-                        dem_pending = true;
-                        res_prev = res;
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < NC; i++) {
-                    dp2[i] = dp[i];
-                    dp[i] = dk[i];
-                }
-                iters = s;
-            }
-            if (outcome == 1) {
-                write_two<NC>(io, m, th, x, y, pl.Z, pv.Z);
-            } else if (outcome == 2) {
-                st |= ST_COLLAPSE;
-                write_single<NC>(io, m, z);
-            } else if (outcome == 3) {
-                st |= ST_NONFINITE;
-                write_single<NC>(io, m, z);
-            } else {
-                // trust-region start: the last evaluated SS point, or the
-                // material-balance point at theta = 1/2 for a negative flash
-                st |= ST_SPLIT_TR;
-                const bool inside = th > 0.0 && th < 1.0;
-#pragma unroll
-                for (int i = 0; i < NC; i++)
-                    ws.nV[i * n + m] = inside ? th * y[i] : 0.5 * K[i] * z[i] / (1.0 + 0.5 * (K[i] - 1.0));
-                need_tr = true;
-            }
-            io.status[m] = st;
-            if (io.iters) io.iters[m] = (io.iters[m] & ~0xff) | (iters & 0xff);
+            for (int i = 0; i < NC; i++) gt[i] = lnK[i] + pv.lnphi[i] - pl.lnphi[i];
+            res = maxabs<NC>(gt);
+            if (!(res < INFINITY)) fail = 2;
         }
+        const int this_it = it++;
+        if (dem_pending && (fail || !(res < res_prev))) {  // undo the accelerated update
+            dem_pending = false;
+#pragma unroll
+            for (int i = 0; i < NC; i++) lnK[i] -= dp[i] * dem_f;
+            return 0;  // the next step re-evaluates the plain update
+        }
+        dem_pending = false;
+        if (fail == 1) {
+            finish(io, ST_COLLAPSE);
+            write_single<NC>(io, m, z);
+            return 1;
+        }
+        if (fail == 2) {
+            finish(io, ST_NONFINITE);
+            write_single<NC>(io, m, z);
+            return 1;
+        }
+        if (fail == 0 && res <= kTolFug) {
+            if (th > 0.0 && th < 1.0) {
+                finish(io, 0);
+                write_two<NC>(io, m, th, x, y, pl.Z, pv.Z);
+            } else {
+                finish(io, ST_COLLAPSE);
+                write_single<NC>(io, m, z);
+            }
+            return 1;
+        }
+        if (this_it >= kSSSplit) {
+            // trust-region start: the last evaluated SS point, or the
+            // material-balance point at theta = 1/2 for a negative flash
+            const bool inside = th > 0.0 && th < 1.0;
+#pragma unroll
+            for (int i = 0; i < NC; i++)
+                ws.nV[i * n + m] = inside ? th * y[i] : 0.5 * K[i] * z[i] / (1.0 + 0.5 * (K[i] - 1.0));
+            finish(io, ST_SPLIT_TR);
+            return 2;
+        }
+        double dk[NC];
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            dk[i] = -gt[i];
+            lnK[i] += dk[i];
+        }
+        const int s = iters + 1;
+        if (s % 5 == 0) {
+            const double f = dem_factor<NC>(dk, dp, dp2);
+            if (f > 0.0) {
+#pragma unroll
+                for (int i = 0; i < NC; i++) lnK[i] += dk[i] * f;
+                dem_f = f;
+                dem_pending = true;
+                res_prev = res;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            dp2[i] = dp[i];
+            dp[i] = dk[i];
+        }
+        iters = s;
+        return 0;
     }
-    return need_tr;
-}
+};
 
 template <int NC>
 __global__ void __launch_bounds__(128) k_split_ss(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_SPLIT);
-    PTF_WARP_ROUNDS(len, qi, valid) {
-        const int64_t m = valid ? ws.q_split[qi] : 0;
-        const bool need_tr = valid ? split_ss_item<NC>(cp, ws, io, m) : false;
-        warp_append(ws.cnt + Q_SPLIT_TR, ws.q_split_tr, need_tr, (int32_t)m);
+    SplitSS<NC> s;
+    bool have = false, drained = false;
+    for (;;) {
+        const int64_t pos = warp_fetch(ws.cnt + H_SPLIT, !have, len, drained);
+        if (pos >= 0) {
+            s.begin(cp, ws, io, ws.q_split[pos]);
+            have = true;
+        }
+        if (!__any_sync(0xffffffffu, have)) break;
+        const int r = have ? s.step(cp, ws, io) : 0;
+        warp_append(ws.cnt + Q_SPLIT_TR, ws.q_split_tr, r == 2, (int32_t)s.m);
+        if (r) have = false;
     }
 }
 

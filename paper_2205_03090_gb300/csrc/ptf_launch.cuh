@@ -10,20 +10,42 @@ namespace ptf {
 // stability TR, decide (or stability output), split SS, split TR.
 constexpr int kStages = 6;
 
+// Blocks of 128 threads for a persistent (refill) kernel: as many as fit on
+// the device at once.
+template <class Kernel>
+int persistent_grid(Kernel k, int sms) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, 128, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return sms * b;
+}
+
 // mode 0: plain flash; mode 1: stability only.  ev (optional, kStages + 1
-// events) is recorded before each stage kernel and after the last one.
+// events) is recorded before each stage and after the last one.  `grid` is
+// the grid of the one-pass kernels; the persistent kernels are sized to the
+// device (sms = grid / 8).
 template <int NC>
 cudaError_t launch_plain(const CompHost& h, const WS& ws, const IO& io, int grid, int mode, cudaStream_t s,
                          cudaEvent_t* ev) {
     const Comp<NC> cp = make_comp<NC>(h);
+    const int sms = grid / 8 > 0 ? grid / 8 : 1;
+    static const int g_pre = persistent_grid(k_precheck<NC>, sms);
+    static const int g_sss = persistent_grid(k_stab_ss<NC>, sms);
+    static const int g_sps = persistent_grid(k_split_ss<NC>, sms);
     auto mark = [&](int k) {
         if (ev) cudaEventRecord(ev[k], s);
     };
     mark(0);
-    if (mode == 0) k_prep_precheck<NC, true><<<grid, 128, 0, s>>>(cp, ws, io);
-    else k_prep_precheck<NC, false><<<grid, 128, 0, s>>>(cp, ws, io);
+    if (mode == 0) {
+        k_prep<NC, true><<<grid, 128, 0, s>>>(cp, ws, io);
+        k_precheck<NC><<<g_pre, 128, 0, s>>>(cp, ws, io);
+    } else {
+        k_prep<NC, false><<<grid, 128, 0, s>>>(cp, ws, io);
+    }
     mark(1);
-    k_stab_ss<NC><<<grid, 128, 0, s>>>(cp, ws, io);
+    k_stab_ss<NC><<<g_sss, 128, 0, s>>>(cp, ws, io);
     mark(2);
     k_stab_tr<NC><<<grid, 128, 0, s>>>(cp, ws, io);
     mark(3);
@@ -31,7 +53,7 @@ cudaError_t launch_plain(const CompHost& h, const WS& ws, const IO& io, int grid
     else k_stab_out<NC><<<grid, 128, 0, s>>>(cp, ws, io);
     mark(4);
     if (mode == 0) {
-        k_split_ss<NC><<<grid, 128, 0, s>>>(cp, ws, io);
+        k_split_ss<NC><<<g_sps, 128, 0, s>>>(cp, ws, io);
         mark(5);
         k_split_tr<NC><<<grid, 128, 0, s>>>(cp, ws, io);
         mark(6);
