@@ -171,6 +171,15 @@ int ptflash_flash_noalloc(int nc, const double* Tc, const double* Pc, const doub
                           double* beta, double* x, double* y, double* K, int32_t* status, int32_t* iters,
                           void* stream);
 
+/*
+ * Self-check of the library's own table-driven logarithm (used on every hot
+ * path) against the CUDA math library's log, on the current device:
+ * 2n inputs (log-uniform over [1e-300, 1e300] and uniform over [0.5, 2]);
+ * *max_ulp_log receives the largest error in units of the last place.
+ * Allocates a few bytes of device memory and synchronises the device.
+ */
+int ptflash_check_math(int64_t n, double* max_ulp_log);
+
 /* Human-readable name of an error code. */
 const char* ptflash_strerror(int code);
 

@@ -14,6 +14,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ptf_logtab.cuh"
+
 namespace ptf {
 
 // ---------------------------------------------------------------------------
@@ -55,6 +57,46 @@ struct Comp {
     double Tc[NC], Pc[NC], lnPc[NC], mi[NC], wc[NC];  // wc = 5.373 (1 + omega)
 };
 
+// ---------------------------------------------------------------------------
+// Natural logarithm for positive normal doubles by a table-driven reduction
+// (P. T. P. Tang, ACM TOMS 16 (1990) 378): x = 2^e m, m in [0.75, 1.5),
+// nearest breakpoint F = 0.75 + j/128, r = (m - F)/F with |r| <= 1/192, and
+// ln x = e ln 2 + ln F + ln(1 + r), ln(1 + r) by its Taylor series to r^7
+// (truncation below 1e-19).  Exponent, mantissa, index and F come from
+// integer operations; m - F is exact (Sterbenz).  About 12 FP64 operations
+// against ~36 FP64 pipe slots of the library log on this GPU.  Zero,
+// negative, subnormal, infinite and NaN inputs go to the library log.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double log_fast(double x) {
+    const long long b = __double_as_longlong(x);
+    if ((unsigned long long)(b - 0x0010000000000000LL) >= 0x7fe0000000000000ULL) return log(x);
+    long long e = (b >> 52) - 1023;
+    const long long frac = b & 0x000fffffffffffffLL;
+    long long mb, fb;
+    int j;
+    if (frac >= 0x0008000000000000LL) {  // m >= 1.5: use m / 2 in [0.75, 1)
+        e += 1;
+        mb = frac | 0x3fe0000000000000LL;
+        j = (int)((frac + (1LL << 45)) >> 46) - 32;                  // round((m/2 - 0.75) 128)
+        fb = 0x3fe0000000000000LL + ((long long)(32 + j) << 46);     // F = (1.5 + j/64) / 2
+    } else {                            // m in [1, 1.5)
+        mb = frac | 0x3ff0000000000000LL;
+        j = 32 + (int)((frac + (1LL << 44)) >> 45);                  // round((m - 0.75) 128)
+        fb = 0x3ff0000000000000LL + ((long long)(j - 32) << 45);     // F = 1 + (j - 32)/128
+    }
+    const double m = __longlong_as_double(mb), F = __longlong_as_double(fb);
+    const double invF = __ldg(&kLogTab[j][0]), lnF = __ldg(&kLogTab[j][1]);
+    const double r = (m - F) * invF;
+    double t = fma(r, 1.0 / 7.0, -1.0 / 6.0);
+    t = fma(t, r, 0.2);
+    t = fma(t, r, -0.25);
+    t = fma(t, r, 1.0 / 3.0);
+    t = fma(t, r, -0.5);
+    const double l1p = fma(t, r * r, r);
+    const double ed = __longlong_as_double(0x4338000000000000LL + e) - 6755399441055744.0;  // (double)e
+    return fma(ed, 0.6931471805599453, lnF + l1p);
+}
+
 // Per-mixture EOS constants: sqrt(A_i) and B_i (reduced, R cancels).
 template <int NC>
 struct Mix {
@@ -81,7 +123,7 @@ __device__ __forceinline__ void mix_init(const Comp<NC>& cp, double P, double T,
 // Eq. wilson
 template <int NC>
 __device__ __forceinline__ void wilson(const Comp<NC>& cp, double P, double T, double* lnK) {
-    double lnP = log(P), invT = 1.0 / T;
+    double lnP = log_fast(P), invT = 1.0 / T;
 #pragma unroll
     for (int i = 0; i < NC; i++) lnK[i] = cp.lnPc[i] - lnP + cp.wc[i] * (1.0 - cp.Tc[i] * invT);
 }
@@ -170,12 +212,12 @@ __device__ __forceinline__ Root cubic_select(double A, double B) {
         if (dv != 0.0) zv -= cub_f(zv, r1, r0) / dv;
     }
     Root r;
-    const double lzbv = log(zv - B), Lv = log(1.0 + B / zv);
+    const double lzbv = log_fast(zv - B), Lv = log_fast(1.0 + B / zv);
     r.Z = zv;
     r.lzb = lzbv;
     r.L = Lv;
     if (zl > B && zl < zv) {
-        const double lzbl = log(zl - B), Ll = log(1.0 + B / zl);
+        const double lzbl = log_fast(zl - B), Ll = log_fast(1.0 + B / zl);
         const double AB = A / B;
         const double gl = zl - lzbl - AB * Ll, gv = zv - lzbv - AB * Lv;
         if (gl < gv) {
@@ -242,28 +284,34 @@ __device__ __forceinline__ void dlnphi_dn(const Comp<NC>& cp, const Mix<NC>& mx,
     const double FZ = fma(fma(3.0, Z, -2.0), Z, A - B - B * B);
     const double FA = Z - B, FB = -Z - 2.0 * B * Z - A;
     const double invFZ = 1.0 / FZ;
-    double Zk[NC], Lk[NC], e[NC], bb[NC];
+    const double cL = 2.0 * L * invB;  // 2 L / B
+    const double Zm1 = Z - 1.0;
     // Zc = sum c_k Z_k, Lc = sum c_k L_k
     const double Zc = -(FA * 2.0 * A + FB * B) * invFZ;
     const double Lc = (Zc + B) * invZpB - Zc * invZ;
+    // f_ij = bb_i p_j + q_j + psi_i w_j + e_i L_j - cL Ahat_ij with
+    //   p_j = Z_j - bb_j (Z - 1) + cL (psi_j - A bb_j), q_j = -(Z_j - B_j)/(Z - B),
+    //   w_j = cL bb_j; the row sum of c_k f_ik is s_i (closed form).
+    double bb[NC], p[NC], q[NC], w[NC], e[NC], Lk[NC], sAc[NC];
 #pragma unroll
     for (int k = 0; k < NC; k++) {
-        Zk[k] = -(FA * 2.0 * ph.psi[k] + FB * mx.B[k]) * invFZ;
-        Lk[k] = (Zk[k] + mx.B[k]) * invZpB - Zk[k] * invZ;
+        const double Zk = -(FA * 2.0 * ph.psi[k] + FB * mx.B[k]) * invFZ;
+        Lk[k] = (Zk + mx.B[k]) * invZpB - Zk * invZ;
         bb[k] = mx.B[k] * invB;
         e[k] = (A * bb[k] - 2.0 * ph.psi[k]) * invB;
+        p[k] = Zk - bb[k] * Zm1 + cL * (ph.psi[k] - A * bb[k]);
+        q[k] = -(Zk - mx.B[k]) * invZB;
+        w[k] = cL * bb[k];
+        sAc[k] = cL * mx.sA[k];
     }
-    const double Zm1 = Z - 1.0;
+    const double qc = (Zc - B) * invZB;
 #pragma unroll
     for (int i = 0; i < NC; i++) {
-        // row constant: -(sum_k c_k f_ik) + terms independent of j
-        const double si = -bb[i] * Zm1 + bb[i] * Zc - (Zc - B) * invZB + e[i] * Lc;
+        const double si = bb[i] * (Zc - Zm1) - qc + e[i] * Lc;
 #pragma unroll
         for (int j = 0; j <= i; j++) {
-            double aij = (i == j) ? mx.sA[i] * mx.sA[i] : cp.kk[i * NC + j] * mx.sA[i] * mx.sA[j];
-            double de = 2.0 * invB * (ph.psi[j] * bb[i] - A * bb[i] * bb[j] - aij + ph.psi[i] * bb[j]);
-            double f = -bb[i] * bb[j] * Zm1 + bb[i] * Zk[j] - (Zk[j] - mx.B[j]) * invZB + de * L + e[i] * Lk[j];
-            J[i * (i + 1) / 2 + j] = f - si;
+            const double ah = (i == j) ? sAc[i] * mx.sA[i] : cp.kk[i * NC + j] * sAc[i] * mx.sA[j];
+            J[i * (i + 1) / 2 + j] = fma(bb[i], p[j], fma(ph.psi[i], w[j], fma(e[i], Lk[j], q[j] - si - ah)));
         }
     }
 }

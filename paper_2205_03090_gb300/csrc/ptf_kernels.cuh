@@ -141,7 +141,7 @@ __device__ __forceinline__ int prep_item(const Comp<NC>& cp, const WS& ws, const
     bool finite = true;
 #pragma unroll
     for (int i = 0; i < NC; i++) {
-        const double lz = log(z[i]);
+        const double lz = log_fast(z[i]);
         const double d = lz + pz.lnphi[i];
         finite = finite && isfinite(d);
         ws.sA[i * n + m] = mx.sA[i];
@@ -225,8 +225,8 @@ struct PrecheckSS {
 #pragma unroll
         for (int i = 0; i < NC; i++) {
             const double d = ws.d[i * n + m];
-            tx = fma(x[i], log(x[i]) + pl.lnphi[i] - d, tx);
-            ty = fma(y[i], log(y[i]) + pv.lnphi[i] - d, ty);
+            tx = fma(x[i], log_fast(x[i]) + pl.lnphi[i] - d, tx);
+            ty = fma(y[i], log_fast(y[i]) + pv.lnphi[i] - d, ty);
         }
         const double dG = (1.0 - th) * tx + th * ty;
         if (!(tx < -kEpsNeg || ty < -kEpsNeg || dG < -kEpsNeg)) {
@@ -436,81 +436,115 @@ __device__ __forceinline__ bool stab_point(const Comp<NC>& cp, const Mix<NC>& mx
     return true;
 }
 
+// One step = one evaluation (EOS and d ln phi / dn) of one trial: the start
+// point, or the trial point of a trust-region iteration.
 template <int NC>
-__device__ __forceinline__ void stab_tr_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t item) {
-    const int64_t n = ws.n;
-    {
-        {
-            const int64_t m = ws.q_stab[item >> 1];
-            const int t = (int)(item & 1);
-            Mix<NC> mx;
-            load_mix<NC>(ws, m, mx);
-            double d[NC];
-            StabPt<NC> cur, nxt;
+struct StabTR {
+    int64_t m, item;
+    int t, it, iters, phase;  // phase 0: evaluate the start point; 1: iterate
+    int32_t fl;
+    Mix<NC> mx;
+    double d[NC], beta[NC], radius;
+    StabPt<NC> cur;
+
+    __device__ __forceinline__ void begin(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t it_) {
+        const int64_t n = ws.n;
+        item = it_;
+        m = ws.q_stab[item >> 1];
+        t = (int)(item & 1);
+        load_mix<NC>(ws, m, mx);
 #pragma unroll
-            for (int i = 0; i < NC; i++) {
-                d[i] = ws.d[i * n + m];
-                cur.lnW[i] = ws.lnW[(t * NC + i) * n + m];
+        for (int i = 0; i < NC; i++) {
+            d[i] = ws.d[i * n + m];
+            cur.lnW[i] = ws.lnW[(t * NC + i) * n + m];
+        }
+        fl = ws.tflag[t * n + m];
+        it = iters = phase = 0;
+        radius = -1.0;
+    }
+
+    __device__ __forceinline__ void store(const WS& ws, int maxiter, int nonfinite) {
+        const int64_t n = ws.n;
+#pragma unroll
+        for (int i = 0; i < NC; i++) ws.lnW[(t * NC + i) * n + m] = cur.lnW[i];
+        ws.tm[t * n + m] = nonfinite ? NAN : cur.tm;
+        ws.tflag[t * n + m] = (fl & 0xff) | (iters << 8) | (1 << 16) | (maxiter << 17) | (nonfinite << 18);
+    }
+
+    // 0 continue, 1 done
+    __device__ __forceinline__ int step(const Comp<NC>& cp, const WS& ws, const IO& io) {
+        StabPt<NC> nxt;
+        double u[NC], pred = 0.0;
+        if (phase == 0) {
+#pragma unroll
+            for (int i = 0; i < NC; i++) nxt.lnW[i] = cur.lnW[i];
+        } else {
+            if (cur.tm < -kEpsNeg || maxabs<NC>(cur.g) < kTolStab) {
+                store(ws, 0, 0);
+                return 1;
             }
-            int32_t fl = ws.tflag[t * n + m];
-            int iters = 0, maxiter = 0, nonfinite = 0;
-            double beta[NC], Lf[NC * (NC + 1) / 2], u[NC];
-            if (!stab_point<NC>(cp, mx, d, cur)) {
-                nonfinite = 1;
-                cur.tm = NAN;
-            } else {
-#pragma unroll
-                for (int i = 0; i < NC; i++) beta[i] = 2.0 * exp(0.5 * cur.lnW[i]);
-                double radius = -1.0;
-#pragma unroll 1
-                for (int it = 0;; it++) {
-                    if (cur.tm < -kEpsNeg) break;
-                    if (maxabs<NC>(cur.g) < kTolStab) break;
-                    if (it == kTRStab) { maxiter = 1; break; }
-                    if (radius < 0.0) {
-                        if (newton_scaled<NC>(cur.H, cur.g, Lf, u)) {
-                            double s = 0.0;
-                            for (int i = 0; i < NC; i++) s = fma(u[i], u[i], s);
-                            radius = sqrt(s);
-                        } else {
-                            radius = 1.0;
-                        }
-                    }
-                    tr_step_scaled<NC>(cur.H, cur.g, radius, Lf, u);
-                    double pred = 0.0;
-                    for (int i = 0; i < NC; i++) {
-                        double hd = 0.0;
-                        for (int j = 0; j < NC; j++) hd = fma(cur.H[i >= j ? tri(i, j) : tri(j, i)], u[j], hd);
-                        pred = fma(cur.g[i], u[i], fma(0.5 * u[i], hd, pred));
-                    }
-#pragma unroll
-                    for (int i = 0; i < NC; i++) nxt.lnW[i] = 2.0 * log(0.5 * fabs(beta[i] + u[i]));
-                    bool ok = stab_point<NC>(cp, mx, d, nxt);
-                    bool trusted = fabs(pred) > kPredTrust * (1.0 + fabs(cur.tm));
-                    double rho = !ok ? -1.0 : (trusted ? (nxt.tm - cur.tm) / pred : 0.5);
-                    if (rho > 0.0) {
-#pragma unroll
-                        for (int i = 0; i < NC; i++) beta[i] = fabs(beta[i] + u[i]);
-                        cur = nxt;
-                    }
-                    if (rho <= 0.25) radius *= 0.5;
-                    else if (rho >= 0.75) radius *= 2.0;
-                    iters = it + 1;
+            if (it == kTRStab) {
+                store(ws, 1, 0);
+                return 1;
+            }
+            double Lf[NC * (NC + 1) / 2];
+            if (radius < 0.0) {
+                if (newton_scaled<NC>(cur.H, cur.g, Lf, u)) {
+                    double s2 = 0.0;
+                    for (int i = 0; i < NC; i++) s2 = fma(u[i], u[i], s2);
+                    radius = sqrt(s2);
+                } else {
+                    radius = 1.0;
                 }
             }
+            tr_step_scaled<NC>(cur.H, cur.g, radius, Lf, u);
+            for (int i = 0; i < NC; i++) {
+                double hd = 0.0;
+                for (int j = 0; j < NC; j++) hd = fma(cur.H[i >= j ? tri(i, j) : tri(j, i)], u[j], hd);
+                pred = fma(cur.g[i], u[i], fma(0.5 * u[i], hd, pred));
+            }
 #pragma unroll
-            for (int i = 0; i < NC; i++) ws.lnW[(t * NC + i) * n + m] = cur.lnW[i];
-            ws.tm[t * n + m] = cur.tm;
-            ws.tflag[t * n + m] = (fl & 0xff) | (iters << 8) | (1 << 16) | (maxiter << 17) | (nonfinite << 18);
+            for (int i = 0; i < NC; i++) nxt.lnW[i] = 2.0 * log_fast(0.5 * fabs(beta[i] + u[i]));
         }
+        const bool ok = stab_point<NC>(cp, mx, d, nxt);
+        if (phase == 0) {
+            if (!ok) {
+                store(ws, 0, 1);
+                return 1;
+            }
+            cur = nxt;
+#pragma unroll
+            for (int i = 0; i < NC; i++) beta[i] = 2.0 * exp(0.5 * cur.lnW[i]);
+            phase = 1;
+            return 0;
+        }
+        const bool trusted = fabs(pred) > kPredTrust * (1.0 + fabs(cur.tm));
+        const double rho = !ok ? -1.0 : (trusted ? (nxt.tm - cur.tm) / pred : 0.5);
+        if (rho > 0.0) {
+#pragma unroll
+            for (int i = 0; i < NC; i++) beta[i] = fabs(beta[i] + u[i]);
+            cur = nxt;
+        }
+        if (rho <= 0.25) radius *= 0.5;
+        else if (rho >= 0.75) radius *= 2.0;
+        iters = ++it;
+        return 0;
     }
-}
+};
 
 template <int NC>
 __global__ void __launch_bounds__(128) k_stab_tr(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_STAB_TR);
-    PTF_WARP_ROUNDS(len, qi, valid) {
-        if (valid) stab_tr_item<NC>(cp, ws, io, ws.q_stab_tr[qi]);
+    StabTR<NC> s;
+    bool have = false, drained = false;
+    for (;;) {
+        const int64_t pos = warp_fetch(ws.cnt + H_STAB_TR, !have, len, drained);
+        if (pos >= 0) {
+            s.begin(cp, ws, io, ws.q_stab_tr[pos]);
+            have = true;
+        }
+        if (!__any_sync(0xffffffffu, have)) break;
+        if (have && s.step(cp, ws, io)) have = false;
     }
 }
 
@@ -745,7 +779,7 @@ __device__ __forceinline__ bool split_point(const Comp<NC>& cp, const Mix<NC>& m
     double G = 0.0;
 #pragma unroll
     for (int i = 0; i < NC; i++) {
-        double mul = log(p.x[i]) + pl.lnphi[i], muv = log(p.y[i]) + pv.lnphi[i];
+        double mul = log_fast(p.x[i]) + pl.lnphi[i], muv = log_fast(p.y[i]) + pv.lnphi[i];
         p.gt[i] = muv - mul;
         G = fma(z[i] - nV[i], mul, fma(nV[i], muv, G));
     }
@@ -780,117 +814,148 @@ __device__ __forceinline__ double boundary_cut(const double* z, const double* nV
     return tau;
 }
 
+// One step = one evaluation of both phases with their derivatives: the start
+// point, a trust-region trial point, or a Newton-polish point.
 template <int NC>
-__device__ __forceinline__ void split_tr_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t m) {
-    const int64_t n = ws.n;
-    {
-        {
-            Mix<NC> mx;
-            load_mix<NC>(ws, m, mx);
-            double z[NC], nV[NC];
+struct SplitTR {
+    int64_t m;
+    int it, iters, newton_steps, phase;  // phase 0: start point; 1: trust region; 2: Newton polish
+    int32_t st;
+    Mix<NC> mx;
+    double z[NC], nV[NC], radius;
+    SplitPt<NC> cur;
+
+    __device__ __forceinline__ void begin(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t mm) {
+        const int64_t n = ws.n;
+        m = mm;
+        load_mix<NC>(ws, m, mx);
 #pragma unroll
-            for (int i = 0; i < NC; i++) {
-                z[i] = io.z[i * io.ld + m];
-                nV[i] = ws.nV[i * n + m];
-            }
-            int32_t st = io.status[m];
-            SplitPt<NC> cur, nxt;
-            double Lf[NC * (NC + 1) / 2], u[NC], dstep[NC];
-            int iters = 0;
-            bool nonfinite = !split_point<NC>(cp, mx, z, nV, cur);
-            if (!nonfinite) {
-                double radius = -1.0;
-                int it = 0, newton_steps = 0;
-                bool phase_newton = false;
-#pragma unroll 1
-                for (int guard = 0; guard < 64; guard++) {
-                    double res = maxabs<NC>(cur.gt);
-                    if (phase_newton) {
-                        if (res <= kTolFug && newton_steps >= 1) break;
-                        if (newton_steps == kNewtonPolish) { st |= ST_MAXITER; break; }
-                    } else if (res < kTolSplitTR) {
-                        phase_newton = true;
-                        continue;
-                    }
-                    if (!phase_newton && it == kTRSplit) { st |= ST_MAXITER; break; }
-                    if (phase_newton) {
-                        if (!newton_scaled<NC>(cur.Hs, cur.gs, Lf, u)) {
-                            if (res > kTolFug) st |= ST_MAXITER;
-                            break;
-                        }
-#pragma unroll
-                        for (int i = 0; i < NC; i++) dstep[i] = cur.S[i] * u[i];
-                        double tau = boundary_cut<NC>(z, nV, dstep);
-#pragma unroll
-                        for (int i = 0; i < NC; i++) nV[i] += tau * dstep[i];
-                        if (!split_point<NC>(cp, mx, z, nV, cur)) { nonfinite = true; break; }
-                        newton_steps++;
-                        iters++;
-                        continue;
-                    }
-                    if (radius < 0.0) {
-                        if (newton_scaled<NC>(cur.Hs, cur.gs, Lf, u)) {
-                            double s = 0.0;
-                            for (int i = 0; i < NC; i++) s = fma(u[i], u[i], s);
-                            radius = sqrt(s);
-                        } else {
-                            radius = 1.0;
-                        }
-                    }
-                    tr_step_scaled<NC>(cur.Hs, cur.gs, radius, Lf, u);
-#pragma unroll
-                    for (int i = 0; i < NC; i++) dstep[i] = cur.S[i] * u[i];
-                    double tau = boundary_cut<NC>(z, nV, dstep);
-                    if (tau < 1.0) {
-#pragma unroll
-                        for (int i = 0; i < NC; i++) {
-                            u[i] *= tau;
-                            dstep[i] *= tau;
-                        }
-                    }
-                    double pred = 0.0;
-                    for (int i = 0; i < NC; i++) {
-                        double hd = 0.0;
-                        for (int j = 0; j < NC; j++) hd = fma(cur.Hs[i >= j ? tri(i, j) : tri(j, i)], u[j], hd);
-                        pred = fma(cur.gs[i], u[i], fma(0.5 * u[i], hd, pred));
-                    }
-                    double nVn[NC];
-#pragma unroll
-                    for (int i = 0; i < NC; i++) nVn[i] = nV[i] + dstep[i];
-                    bool ok = split_point<NC>(cp, mx, z, nVn, nxt);
-                    bool trusted = fabs(pred) > kPredTrust * (1.0 + fabs(cur.G));
-                    double rho = !ok ? -1.0 : (trusted ? (nxt.G - cur.G) / pred : 0.5);
-                    if (rho > 0.0) {
-#pragma unroll
-                        for (int i = 0; i < NC; i++) nV[i] = nVn[i];
-                        cur = nxt;
-                    }
-                    if (rho <= 0.25) radius *= 0.5;
-                    else if (rho >= 0.75) radius *= 2.0;
-                    it++;
-                    iters = it;
-                }
-            }
-            if (nonfinite) {
-                st |= ST_NONFINITE;
-                write_single<NC>(io, m, z);
-            } else if (!(cur.th > 0.0 && cur.th < 1.0)) {
-                st |= ST_COLLAPSE;
-                write_single<NC>(io, m, z);
-            } else {
-                write_two<NC>(io, m, cur.th, cur.x, cur.y, cur.ZL, cur.ZV);
-            }
-            io.status[m] = st;
-            if (io.iters) io.iters[m] = (io.iters[m] & ~0xff00) | ((iters & 0xff) << 8);
+        for (int i = 0; i < NC; i++) {
+            z[i] = io.z[i * io.ld + m];
+            nV[i] = ws.nV[i * n + m];
         }
+        st = io.status[m];
+        it = iters = newton_steps = phase = 0;
+        radius = -1.0;
     }
-}
+
+    __device__ __forceinline__ int finish(const IO& io, int kind) {  // kind 0 result, 1 non-finite
+        if (kind == 1) {
+            st |= ST_NONFINITE;
+            write_single<NC>(io, m, z);
+        } else if (!(cur.th > 0.0 && cur.th < 1.0)) {
+            st |= ST_COLLAPSE;
+            write_single<NC>(io, m, z);
+        } else {
+            write_two<NC>(io, m, cur.th, cur.x, cur.y, cur.ZL, cur.ZV);
+        }
+        io.status[m] = st;
+        if (io.iters) io.iters[m] = (io.iters[m] & ~0xff00) | ((iters & 0xff) << 8);
+        return 1;
+    }
+
+    // 0 continue, 1 done
+    __device__ __forceinline__ int step(const Comp<NC>& cp, const WS& ws, const IO& io) {
+        double Lf[NC * (NC + 1) / 2], u[NC], dstep[NC], trial[NC], pred = 0.0;
+        if (phase == 0) {
+#pragma unroll
+            for (int i = 0; i < NC; i++) trial[i] = nV[i];
+        } else {
+            const double res = maxabs<NC>(cur.gt);
+            if (phase == 1 && res < kTolSplitTR) phase = 2;
+            if (phase == 2) {
+                if (res <= kTolFug && newton_steps >= 1) return finish(io, 0);
+                if (newton_steps == kNewtonPolish) {
+                    st |= ST_MAXITER;
+                    return finish(io, 0);
+                }
+                if (!newton_scaled<NC>(cur.Hs, cur.gs, Lf, u)) {
+                    if (res > kTolFug) st |= ST_MAXITER;
+                    return finish(io, 0);
+                }
+#pragma unroll
+                for (int i = 0; i < NC; i++) dstep[i] = cur.S[i] * u[i];
+                const double tau = boundary_cut<NC>(z, nV, dstep);
+#pragma unroll
+                for (int i = 0; i < NC; i++) trial[i] = nV[i] + tau * dstep[i];
+            } else {
+                if (it == kTRSplit) {
+                    st |= ST_MAXITER;
+                    return finish(io, 0);
+                }
+                if (radius < 0.0) {
+                    if (newton_scaled<NC>(cur.Hs, cur.gs, Lf, u)) {
+                        double s2 = 0.0;
+                        for (int i = 0; i < NC; i++) s2 = fma(u[i], u[i], s2);
+                        radius = sqrt(s2);
+                    } else {
+                        radius = 1.0;
+                    }
+                }
+                tr_step_scaled<NC>(cur.Hs, cur.gs, radius, Lf, u);
+#pragma unroll
+                for (int i = 0; i < NC; i++) dstep[i] = cur.S[i] * u[i];
+                const double tau = boundary_cut<NC>(z, nV, dstep);
+                if (tau < 1.0) {
+#pragma unroll
+                    for (int i = 0; i < NC; i++) {
+                        u[i] *= tau;
+                        dstep[i] *= tau;
+                    }
+                }
+                for (int i = 0; i < NC; i++) {
+                    double hd = 0.0;
+                    for (int j = 0; j < NC; j++) hd = fma(cur.Hs[i >= j ? tri(i, j) : tri(j, i)], u[j], hd);
+                    pred = fma(cur.gs[i], u[i], fma(0.5 * u[i], hd, pred));
+                }
+#pragma unroll
+                for (int i = 0; i < NC; i++) trial[i] = nV[i] + dstep[i];
+            }
+        }
+        SplitPt<NC> nxt;
+        const bool ok = split_point<NC>(cp, mx, z, trial, nxt);
+        if (phase == 0) {
+            if (!ok) return finish(io, 1);
+            cur = nxt;
+            phase = 1;
+            return 0;
+        }
+        if (phase == 2) {  // Newton polish steps are taken unconditionally
+            if (!ok) return finish(io, 1);
+#pragma unroll
+            for (int i = 0; i < NC; i++) nV[i] = trial[i];
+            cur = nxt;
+            newton_steps++;
+            iters++;
+            return 0;
+        }
+        const bool trusted = fabs(pred) > kPredTrust * (1.0 + fabs(cur.G));
+        const double rho = !ok ? -1.0 : (trusted ? (nxt.G - cur.G) / pred : 0.5);
+        if (rho > 0.0) {
+#pragma unroll
+            for (int i = 0; i < NC; i++) nV[i] = trial[i];
+            cur = nxt;
+        }
+        if (rho <= 0.25) radius *= 0.5;
+        else if (rho >= 0.75) radius *= 2.0;
+        iters = ++it;
+        return 0;
+    }
+};
 
 template <int NC>
 __global__ void __launch_bounds__(128) k_split_tr(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_SPLIT_TR);
-    PTF_WARP_ROUNDS(len, qi, valid) {
-        if (valid) split_tr_item<NC>(cp, ws, io, ws.q_split_tr[qi]);
+    SplitTR<NC> s;
+    bool have = false, drained = false;
+    for (;;) {
+        const int64_t pos = warp_fetch(ws.cnt + H_SPLIT_TR, !have, len, drained);
+        if (pos >= 0) {
+            s.begin(cp, ws, io, ws.q_split_tr[pos]);
+            have = true;
+        }
+        if (!__any_sync(0xffffffffu, have)) break;
+        if (have && s.step(cp, ws, io)) have = false;
     }
 }
 

@@ -34,6 +34,8 @@ cudaError_t launch_plain(const CompHost& h, const WS& ws, const IO& io, int grid
     static const int g_pre = persistent_grid(k_precheck<NC>, sms);
     static const int g_sss = persistent_grid(k_stab_ss<NC>, sms);
     static const int g_sps = persistent_grid(k_split_ss<NC>, sms);
+    static const int g_str = persistent_grid(k_stab_tr<NC>, sms);
+    static const int g_spt = persistent_grid(k_split_tr<NC>, sms);
     auto mark = [&](int k) {
         if (ev) cudaEventRecord(ev[k], s);
     };
@@ -47,7 +49,7 @@ cudaError_t launch_plain(const CompHost& h, const WS& ws, const IO& io, int grid
     mark(1);
     k_stab_ss<NC><<<g_sss, 128, 0, s>>>(cp, ws, io);
     mark(2);
-    k_stab_tr<NC><<<grid, 128, 0, s>>>(cp, ws, io);
+    k_stab_tr<NC><<<g_str, 128, 0, s>>>(cp, ws, io);
     mark(3);
     if (mode == 0) k_stab_decide<NC><<<grid, 128, 0, s>>>(cp, ws, io);
     else k_stab_out<NC><<<grid, 128, 0, s>>>(cp, ws, io);
@@ -55,7 +57,7 @@ cudaError_t launch_plain(const CompHost& h, const WS& ws, const IO& io, int grid
     if (mode == 0) {
         k_split_ss<NC><<<g_sps, 128, 0, s>>>(cp, ws, io);
         mark(5);
-        k_split_tr<NC><<<grid, 128, 0, s>>>(cp, ws, io);
+        k_split_tr<NC><<<g_spt, 128, 0, s>>>(cp, ws, io);
         mark(6);
     } else {
         mark(5);
