@@ -40,6 +40,10 @@ TOL = 1e-8
 LIB_STAGES = ("prep_precheck", "stab_ss", "stab_tr", "stab_decide", "split_ss", "split_tr")
 ORACLE_STAGE = {"prep_precheck": 0, "stab_ss": 1, "stab_tr": 2, "split_ss": 3, "split_tr": 4}
 KERNELS_PER_STEP = 8  # 7 stage kernels + the counter fold
+LEARNED_WORKLOAD = "nc10_2phase_1e7"
+LEARNED_DESC = ("10 SRK pseudo-components drawn as above, 1e7 mixtures, T~U(250,450) K, P~U(2,15) MPa, "
+                "z~Dirichlet(1); classifier 3x64 SiLU and ln K initializer 3x128 SiLU (BF16/FP32), "
+                "p_l=0.02, p_r=0.98")
 
 
 def dist_env():
@@ -237,6 +241,8 @@ def ours_arm(args, ws, rank, local):
     h2d = n * (2 + nc) * 8
     d2h = n * (4 + 8 + 3 * nc * 8 + 4 + 4)
 
+    learned = learned_leg(args, rank, dev, flush, stream) if args.learned_n > 0 else None
+
     if rank != 0:
         if dist:
             dist.barrier()
@@ -287,12 +293,71 @@ def ours_arm(args, ws, rank, local):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clk,
+        "learned": learned,
     }
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def learned_leg(args, rank, dev, flush, stream):
+    """Plain vs learned form (Sec. 4) on the 10-component workload: the same
+    inputs timed through both, the learned result checked against the
+    oracle on a sample.  Uses the committed checkpoint, training one first if
+    there is none."""
+    import torch
+    from paper_2205_03090_gb300 import nn, ptflash, workloads as wl
+    from paper_2205_03090_gb300 import train_nn
+    w = dict(wl.WORKLOADS[LEARNED_WORKLOAD])
+    comp = wl.pseudo_components(w["nc"], w["comp_seed"])
+    n = args.learned_n
+    cond = wl.conditions(w["nc"], n, w["cond_seed"] + 1000 * rank, w["T_range"], w["P_range"], w["alpha"])
+    if not nn.exists(train_nn.DEFAULT_OUT):
+        train_nn.main([])
+    fl = ptflash.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=n)
+    meta = nn.load_checkpoint(fl, train_nn.DEFAULT_OUT)
+    P = torch.tensor(cond.P, device=dev)
+    T = torch.tensor(cond.T, device=dev)
+    z = torch.tensor(cond.z, device=dev).contiguous()
+    out = fl.alloc_outputs(n, dev)
+    res = {}
+    for form in ("plain", "learned"):
+        use = form == "learned"
+        for _ in range(max(1, args.warmup - 1)):
+            fl.ptflash_flash(P, T, z, out=out, use_nn=use, stream=stream)
+        ms = []
+        for _ in range(max(1, args.steps)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fl.ptflash_flash(P, T, z, out=out, use_nn=use, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res[form] = {"ms_per_step": float(np.mean(ms)), "queues": fl.ptflash_last_counts()}
+        if use:
+            g = {k: getattr(out, k).cpu().numpy() for k in ("nphase", "beta", "x", "y", "status")}
+    frac, sample = float("nan"), 0
+    if rank == 0 and args.cpu_sample > 0:
+        rng = np.random.default_rng(13)
+        sample = min(n, max(2000, args.cpu_sample // 5))
+        idx = np.sort(rng.choice(n, sample, replace=False))
+        o, _, s = run_oracle_sample(comp, cond, idx)
+        frac = match_fraction(s, comp, cond, idx, o, g)
+    fl.close()
+    learned_v = n * (frac if frac == frac else 1.0) / (res["learned"]["ms_per_step"] / 1e3)
+    return {"workload": LEARNED_DESC, "n": n, "ms_per_step": res["learned"]["ms_per_step"],
+            "value": learned_v, "unit": "flashes/s",
+            "plain_ms_per_step": res["plain"]["ms_per_step"],
+            "plain_value": n / (res["plain"]["ms_per_step"] / 1e3),
+            "speedup_vs_plain": res["plain"]["ms_per_step"] / res["learned"]["ms_per_step"],
+            "oracle_match": {"frac": frac, "sample": sample, "tol": TOL},
+            "queues_plain": res["plain"]["queues"], "queues_learned": res["learned"]["queues"],
+            "networks": {k: meta.get(k) for k in ("classifier", "initializer", "train_samples")}}
 
 
 def main():
@@ -304,6 +369,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=100_000)
     ap.add_argument("--ref-sample", type=int, default=20_000)
     ap.add_argument("--n", type=int, default=0, help="mixtures per rank (default: the workload's 1e6)")
+    ap.add_argument("--learned-n", type=int, default=10_000_000,
+                    help="mixtures of the learned-form leg (0 skips it)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

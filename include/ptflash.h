@@ -172,6 +172,47 @@ int ptflash_flash_noalloc(int nc, const double* Tc, const double* Pc, const doub
                           void* stream);
 
 /*
+ * Learned form (Sec. 4 of the paper).  which = 0: stability classifier
+ * (3 hidden layers of `hidden` SiLU units, one logit; p = sigmoid(logit) is
+ * the probability that the mixture is stable); which = 1: ln K initializer
+ * (3 hidden layers of `hidden` SiLU units, nc outputs).  Inputs are the nc + 2
+ * features (z_1..z_nc, P, T), standardised as (v - mean) / std (the paper's
+ * scaling layer) and rounded to bfloat16; weights and hidden activations are
+ * bfloat16, sums FP32.  Parameters: one FP32 vector W1, b1, W2, b2, W3, b3,
+ * W4, b4 with each W row-major [out][in] (count: ptflash_nn_param_count(nc + 2,
+ * hidden, dout)).  hidden must be 64 or 128.
+ *
+ * ptflash_nn_set: HOST theta, mean[nc+2], std[nc+2]; copies them, makes the
+ *   bfloat16 compute copy and resets the Adam state.  Components must be set.
+ * ptflash_nn_get: copies the FP32 parameters to HOST theta (synchronises).
+ * ptflash_nn_features: DEVICE X[(nc+2) * n] (row stride n), the standardised
+ *   bfloat16 features of DEVICE P, T, z.
+ * ptflash_nn_infer: DEVICE out[dout * n] network outputs for DEVICE P, T, z.
+ * ptflash_nn_train_steps: `steps` Adam steps (Kingma & Ba; beta1, beta2, eps)
+ *   of `batch` samples each (a multiple of 128).  DEVICE X[(nc+2) * n]
+ *   features, Y targets (classifier: [n], 1 stable / 0 unstable, binary
+ *   cross-entropy on the logit; initializer: [nc * n] ln K, absolute error
+ *   summed over components; both averaged over the batch), perm[steps *
+ *   batch] sample indices, HOST lr[steps] learning rates, optional DEVICE
+ *   loss[steps] (each entry incremented by that step's batch loss; zero it
+ *   first).  The first call allocates training scratch.
+ * ptflash_nn_eval: mean loss and (classifier) accuracy at p = 1/2 over DEVICE
+ *   X[(nc+2) * n], Y (same layouts); synchronises.
+ */
+int64_t ptflash_nn_param_count(int din, int hidden, int dout);
+int ptflash_nn_set(ptflash_ctx* ctx, int which, int hidden, const float* theta, const float* mean, const float* std);
+int ptflash_nn_get(ptflash_ctx* ctx, int which, float* theta);
+int ptflash_nn_features(ptflash_ctx* ctx, int which, int64_t n, const double* P, const double* T, const double* z,
+                        float* X, void* stream);
+int ptflash_nn_infer(ptflash_ctx* ctx, int which, int64_t n, const double* P, const double* T, const double* z,
+                     float* out, void* stream);
+int ptflash_nn_train_steps(ptflash_ctx* ctx, int which, int64_t n, const float* X, const float* Y,
+                           const int32_t* perm, int64_t steps, int batch, const float* lr, float beta1, float beta2,
+                           float eps, float* loss, void* stream);
+int ptflash_nn_eval(ptflash_ctx* ctx, int which, int64_t n, const float* X, const float* Y, double* loss,
+                    double* accuracy, void* stream);
+
+/*
  * Self-check of the library's own table-driven logarithm (used on every hot
  * path) against the CUDA math library's log, on the current device:
  * 2n inputs (log-uniform over [1e-300, 1e300] and uniform over [0.5, 2]);

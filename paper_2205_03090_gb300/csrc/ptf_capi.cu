@@ -7,6 +7,7 @@
 
 #include "../../include/ptflash.h"
 #include "ptf_launch.cuh"
+#include "ptf_ctx.cuh"
 
 using namespace ptf;
 
@@ -24,60 +25,23 @@ int cuda_fail(cudaError_t e) {
     } while (0)
 }  // namespace
 
-struct ptflash_ctx {
-    int device = 0;
-    int nc_max = 0;
-    int64_t n_max = 0;
-    int sm_count = 0;
-    CompHost comp{};
-    bool have_comp = false;
-    // device scratch
-    double* wsd = nullptr;    // (8 nc_max + 3) n_max doubles
-    int32_t* wsi = nullptr;   // 7 n_max + 64 int32
-    // staging for the host-pointer entry point
-    double* hd = nullptr;     // (4 nc_max + 3) n_max doubles: P, T, z, beta, x, y, K
-    int32_t* hi = nullptr;    // 3 n_max: nphase, status, iters
-    unsigned long long* acc = nullptr;  // device: queue sizes summed over the chunks of a call
-    bool profiling = false;
-    cudaEvent_t ev[kStages + 1] = {};
-    double stage_ms[kStages] = {};
-};
-
 // Fold the four queue counters of a chunk into the call's accumulator.
 __global__ void k_fold_counts(const int32_t* cnt, unsigned long long* acc) {
     if (threadIdx.x < 4) acc[threadIdx.x] += (unsigned long long)cnt[threadIdx.x];
 }
 
-static WS make_ws(ptflash_ctx* c, int64_t n) {
-    const int nc = c->comp.nc;
-    WS w;
-    w.n = n;
-    double* p = c->wsd;
-    w.sA = p; p += (int64_t)nc * n;
-    w.B = p; p += (int64_t)nc * n;
-    w.lnz = p; p += (int64_t)nc * n;
-    w.d = p; p += (int64_t)nc * n;
-    w.lnK = p; p += (int64_t)nc * n;
-    w.nV = p; p += (int64_t)nc * n;
-    w.lnW = p; p += 2 * (int64_t)nc * n;
-    w.theta = p; p += n;
-    w.tm = p; p += 2 * n;
-    int32_t* q = c->wsi;
-    w.cnt = q; q += 64;
-    w.tflag = q; q += 2 * n;
-    w.q_stab = q; q += n;
-    w.q_split = q; q += n;
-    w.q_stab_tr = q; q += 2 * n;
-    w.q_split_tr = q; q += n;
-    return w;
-}
-
-static cudaError_t dispatch(ptflash_ctx* c, const WS& ws, const IO& io, int mode, cudaStream_t s) {
+static cudaError_t dispatch(ptflash_ctx* c, const WS& ws, const IO& io, int mode, cudaStream_t s, float p_l = 0.02f,
+                           float p_r = 0.98f) {
     const int grid = c->sm_count * 8;
     cudaEvent_t* ev = c->profiling ? c->ev : nullptr;
+    MLP nn[2];
+    if (mode == 2) {
+        nn[0] = c->nn[0].view();
+        nn[1] = c->nn[1].view();
+    }
     switch (c->comp.nc) {
 #define PTF_CASE(NC) \
-    case NC: return launch_plain<NC>(c->comp, ws, io, grid, mode, s, ev);
+    case NC: return launch_plain<NC>(c->comp, ws, io, grid, mode, s, ev, nn, p_l, p_r);
         PTF_CASE(2) PTF_CASE(3) PTF_CASE(4) PTF_CASE(5) PTF_CASE(6) PTF_CASE(7) PTF_CASE(8) PTF_CASE(9)
         PTF_CASE(10) PTF_CASE(11) PTF_CASE(12) PTF_CASE(13) PTF_CASE(14) PTF_CASE(15) PTF_CASE(16)
 #undef PTF_CASE
@@ -210,7 +174,7 @@ int ptflash_set_components(ptflash_ctx* c, int nc, const double* Tc, const doubl
 
 static int run(ptflash_ctx* c, int64_t n, const double* P, const double* T, const double* z, int32_t* o_i,
                double* o_d, double* x, double* y, double* K, int32_t* status, int32_t* iters, int mode,
-               bool zero_counts, cudaStream_t s) {
+               bool zero_counts, cudaStream_t s, float p_l = 0.02f, float p_r = 0.98f) {
     if (zero_counts) {
         PTF_CUDA(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
         for (int k = 0; k < kStages; k++) c->stage_ms[k] = 0.0;
@@ -231,7 +195,7 @@ static int run(ptflash_ctx* c, int64_t n, const double* P, const double* T, cons
         io.status = status + m0;
         io.iters = iters ? iters + m0 : nullptr;
         PTF_CUDA(cudaMemsetAsync(ws.cnt, 0, 64 * sizeof(int32_t), s));
-        PTF_CUDA(dispatch(c, ws, io, mode, s));
+        PTF_CUDA(dispatch(c, ws, io, mode, s, p_l, p_r));
         k_fold_counts<<<1, 32, 0, s>>>(ws.cnt, c->acc);
         PTF_CUDA(cudaGetLastError());
         if (c->profiling) {  // profiling mode waits for each chunk to read its stage times
@@ -254,8 +218,16 @@ int ptflash_flash(ptflash_ctx* c, int64_t n, const double* P, const double* T, c
     if (n < 0) return PTF_ERR_INVALID_ARG;
     if (n == 0) return PTF_OK;
     if (!P || !T || !z || !nphase || !beta || !x || !y || !K || !status) return PTF_ERR_INVALID_ARG;
-    if (opt && opt->use_nn) return PTF_ERR_NOT_READY;
-    return run(c, n, P, T, z, nphase, beta, x, y, K, status, iters, 0, true, (cudaStream_t)stream);
+    int mode = 0;
+    float p_l = 0.02f, p_r = 0.98f;
+    if (opt && opt->use_nn) {
+        if (!c->nn[0].ready || !c->nn[1].ready) return PTF_ERR_NOT_READY;
+        if (!(opt->p_l >= 0.0 && opt->p_l <= opt->p_r && opt->p_r <= 1.0)) return PTF_ERR_INVALID_ARG;
+        mode = 2;
+        p_l = (float)opt->p_l;
+        p_r = (float)opt->p_r;
+    }
+    return run(c, n, P, T, z, nphase, beta, x, y, K, status, iters, mode, true, (cudaStream_t)stream, p_l, p_r);
 }
 
 int ptflash_stability(ptflash_ctx* c, int64_t n, const double* P, const double* T, const double* z,
@@ -288,7 +260,15 @@ int ptflash_flash_host(ptflash_ctx* c, int64_t n, const double* P, const double*
             return PTF_ERR_NO_MEMORY;
         }
     }
-    if (opt && opt->use_nn) return PTF_ERR_NOT_READY;
+    int mode = 0;
+    float p_l = 0.02f, p_r = 0.98f;
+    if (opt && opt->use_nn) {
+        if (!c->nn[0].ready || !c->nn[1].ready) return PTF_ERR_NOT_READY;
+        if (!(opt->p_l >= 0.0 && opt->p_l <= opt->p_r && opt->p_r <= 1.0)) return PTF_ERR_INVALID_ARG;
+        mode = 2;
+        p_l = (float)opt->p_l;
+        p_r = (float)opt->p_r;
+    }
     PTF_CUDA(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
     for (int64_t m0 = 0; m0 < n; m0 += nm) {
         const int64_t cn = (n - m0 < nm) ? n - m0 : nm;
@@ -306,7 +286,7 @@ int ptflash_flash_host(ptflash_ctx* c, int64_t n, const double* P, const double*
         PTF_CUDA(cudaMemcpyAsync(dP, P + m0, rowb, cudaMemcpyHostToDevice, s));
         PTF_CUDA(cudaMemcpyAsync(dT, T + m0, rowb, cudaMemcpyHostToDevice, s));
         PTF_CUDA(cudaMemcpy2DAsync(dz, rowb, z + m0, pitch, rowb, nc, cudaMemcpyHostToDevice, s));
-        int rc = run(c, cn, dP, dT, dz, dnp, dbeta, dx, dy, dK, dst, iters ? dit : nullptr, 0, false, s);
+        int rc = run(c, cn, dP, dT, dz, dnp, dbeta, dx, dy, dK, dst, iters ? dit : nullptr, mode, false, s, p_l, p_r);
         if (rc) return rc;
         PTF_CUDA(cudaMemcpyAsync(nphase + m0, dnp, cn * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PTF_CUDA(cudaMemcpyAsync(status + m0, dst, cn * sizeof(int32_t), cudaMemcpyDeviceToHost, s));

@@ -2,7 +2,10 @@
 #include <cmath>
 #include "ptf_launch.cuh"
 namespace ptf {
-template cudaError_t launch_plain<14>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*);
-template cudaError_t launch_plain<15>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*);
-template cudaError_t launch_plain<16>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*);
+template cudaError_t launch_plain<14>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*, const MLP*, float,
+                                   float);
+template cudaError_t launch_plain<15>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*, const MLP*, float,
+                                   float);
+template cudaError_t launch_plain<16>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*, const MLP*, float,
+                                   float);
 }  // namespace ptf

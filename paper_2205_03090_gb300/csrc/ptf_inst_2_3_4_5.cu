@@ -2,8 +2,12 @@
 #include <cmath>
 #include "ptf_launch.cuh"
 namespace ptf {
-template cudaError_t launch_plain<2>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*);
-template cudaError_t launch_plain<3>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*);
-template cudaError_t launch_plain<4>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*);
-template cudaError_t launch_plain<5>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*);
+template cudaError_t launch_plain<2>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*, const MLP*, float,
+                                   float);
+template cudaError_t launch_plain<3>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*, const MLP*, float,
+                                   float);
+template cudaError_t launch_plain<4>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*, const MLP*, float,
+                                   float);
+template cudaError_t launch_plain<5>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*, const MLP*, float,
+                                   float);
 }  // namespace ptf

@@ -30,6 +30,8 @@ struct WS {
     int32_t* tflag;    // [2 n]: ss iters | tr iters << 8 | used_tr << 16 | maxiter << 17 | nonfinite << 18
     int32_t *q_stab, *q_split, *q_stab_tr, *q_split_tr;
     int32_t* cnt;      // [0] stab, [1] split, [2] stab_tr (items), [3] split_tr
+    float* nnp = nullptr;  // learned form: classifier logits [n]
+    float* nnk = nullptr;  // learned form: initializer ln K [NC n]
 };
 
 struct IO {
@@ -311,7 +313,12 @@ struct StabSS {
         t = (int)(item & 1);
         load_mix<NC>(ws, m, mx);
         double lnKw[NC];
-        wilson<NC>(cp, io.P[m], io.T[m], lnKw);
+        if (io.status[m] & ST_NN_INIT) {  // learned form: trials from the initializer's K (Sec. 4.3)
+#pragma unroll
+            for (int i = 0; i < NC; i++) lnKw[i] = ws.lnK[i * n + m];
+        } else {
+            wilson<NC>(cp, io.P[m], io.T[m], lnKw);
+        }
 #pragma unroll
         for (int i = 0; i < NC; i++) {
             d[i] = ws.d[i * n + m];
@@ -993,6 +1000,57 @@ __global__ void __launch_bounds__(128) k_stab_out(const __grid_constant__ Comp<N
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_STAB);
     PTF_WARP_ROUNDS(len, qi, valid) {
         if (valid) stab_out_item<NC>(cp, ws, io, ws.q_stab[qi]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Learned form (Sec. 4.3): gate each mixture on the classifier's probability
+// p of being stable.  p >= p_r: single phase; p <= p_l: phase split from the
+// initializer's ln K (if finite and bracketing K = 1); otherwise stability
+// analysis with trials initialised from the initializer's K (Wilson K when
+// the initializer output is not finite).  ln K is clamped to [-15, 15].
+// ---------------------------------------------------------------------------
+template <int NC>
+__global__ void __launch_bounds__(128) k_nn_route(const __grid_constant__ Comp<NC> cp, WS ws, IO io, float p_l,
+                                                  float p_r) {
+    const int64_t n = ws.n;
+    PTF_WARP_ROUNDS(n, m, valid) {
+        int route = 0;
+        if (valid && !(io.status[m] & ST_NONFINITE)) {
+            const float p = 1.0f / (1.0f + __expf(-ws.nnp[m]));
+            double lnK[NC], kmax = -1e300, kmin = 1e300;
+            bool fin = true;
+#pragma unroll
+            for (int i = 0; i < NC; i++) {
+                double v = (double)ws.nnk[i * n + m];
+                fin = fin && isfinite(v);
+                v = fmin(fmax(v, -15.0), 15.0);
+                lnK[i] = v;
+                kmax = fmax(kmax, v);
+                kmin = fmin(kmin, v);
+            }
+            if (p >= p_r) {
+                double z[NC];
+#pragma unroll
+                for (int i = 0; i < NC; i++) z[i] = io.z[i * io.ld + m];
+                io.status[m] = ST_NN_STABLE;
+                write_single<NC>(io, m, z);
+            } else {
+                if (fin) {
+#pragma unroll
+                    for (int i = 0; i < NC; i++) ws.lnK[i * n + m] = lnK[i];
+                }
+                if (p <= p_l && fin && kmax > 0.0 && kmin < 0.0) {
+                    io.status[m] = ST_NN_UNSTABLE | ST_NN_INIT;
+                    route = 2;
+                } else {
+                    io.status[m] = ST_STAB_RUN | (fin ? ST_NN_INIT : 0);
+                    route = 1;
+                }
+            }
+        }
+        warp_append(ws.cnt + Q_STAB, ws.q_stab, route == 1, (int32_t)m);
+        warp_append(ws.cnt + Q_SPLIT, ws.q_split, route == 2, (int32_t)m);
     }
 }
 

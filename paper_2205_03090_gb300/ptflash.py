@@ -60,6 +60,20 @@ def load(path: str = LIB_PATH):
     lib.ptflash_last_counts.argtypes = [_VP, ctypes.POINTER(_I64)]
     lib.ptflash_set_profiling.argtypes = [_VP, ctypes.c_int]
     lib.ptflash_last_stage_ms.argtypes = [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    _F = ctypes.POINTER(ctypes.c_float)
+    lib.ptflash_nn_set.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _F, _F, _F]
+    lib.ptflash_nn_get.argtypes = [_VP, ctypes.c_int, _F]
+    lib.ptflash_nn_param_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.ptflash_nn_param_count.restype = ctypes.c_int64
+    lib.ptflash_nn_features.argtypes = [_VP, ctypes.c_int, _I64, _VP, _VP, _VP, _VP, _VP]
+    lib.ptflash_nn_infer.argtypes = [_VP, ctypes.c_int, _I64, _VP, _VP, _VP, _VP, _VP]
+    lib.ptflash_nn_train_steps.argtypes = [_VP, ctypes.c_int, _I64, _VP, _VP, _VP, _I64, ctypes.c_int, _F,
+                                           ctypes.c_float, ctypes.c_float, ctypes.c_float, _VP, _VP]
+    lib.ptflash_nn_eval.argtypes = [_VP, ctypes.c_int, _I64, _VP, _VP, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), _VP]
+    for f in ("ptflash_nn_set", "ptflash_nn_get", "ptflash_nn_features", "ptflash_nn_infer", "ptflash_nn_train_steps",
+              "ptflash_nn_eval"):
+        getattr(lib, f).restype = ctypes.c_int
     lib.ptflash_strerror.argtypes = [ctypes.c_int]
     lib.ptflash_strerror.restype = ctypes.c_char_p
     lib.ptflash_last_cuda_error.restype = ctypes.c_char_p
@@ -116,6 +130,7 @@ class Flash:
         nc = int(Tc.shape[0])
         self.nc = nc
         self.n_max = int(n_max)
+        self._nn_scaler = {}  # which -> (mean, std) of the network features
         h = _VP()
         _check(lib.ptflash_create(ctypes.byref(h), nc_max or nc, self.n_max))
         self._h = h
@@ -191,6 +206,38 @@ class Flash:
         ms = (ctypes.c_double * 6)()
         _check(load().ptflash_last_stage_ms(self._h, ms, 6))
         return dict(zip(self.STAGES, list(ms)))
+
+    # ---- learned form (Sec. 4): which = 0 classifier, 1 initializer ----
+    def ptflash_nn_set(self, which: int, hidden: int, theta, mean, std):
+        F = ctypes.POINTER(ctypes.c_float)
+        arrs = [np.ascontiguousarray(a, np.float32) for a in (theta, mean, std)]
+        _check(load().ptflash_nn_set(self._h, which, hidden, *[a.ctypes.data_as(F) for a in arrs]))
+
+    def ptflash_nn_get(self, which: int, count: int):
+        out = np.zeros(count, np.float32)
+        _check(load().ptflash_nn_get(self._h, which, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
+    def ptflash_nn_features(self, which, P, T, z, X, stream=None):
+        _check(load().ptflash_nn_features(self._h, which, int(P.shape[0]), _ptr(P), _ptr(T), _ptr(z), _ptr(X),
+                                          _stream_handle(stream)))
+
+    def ptflash_nn_infer(self, which, P, T, z, out, stream=None):
+        _check(load().ptflash_nn_infer(self._h, which, int(P.shape[0]), _ptr(P), _ptr(T), _ptr(z), _ptr(out),
+                                       _stream_handle(stream)))
+
+    def ptflash_nn_train_steps(self, which, X, Y, perm, steps, batch, lr, beta1=0.9, beta2=0.999, eps=1e-8,
+                               loss=None, stream=None):
+        lr = np.ascontiguousarray(lr, np.float32)
+        _check(load().ptflash_nn_train_steps(self._h, which, int(X.shape[1]), _ptr(X), _ptr(Y), _ptr(perm), steps,
+                                             batch, lr.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), beta1, beta2,
+                                             eps, _ptr(loss), _stream_handle(stream)))
+
+    def ptflash_nn_eval(self, which, X, Y, stream=None):
+        l, a = ctypes.c_double(), ctypes.c_double()
+        _check(load().ptflash_nn_eval(self._h, which, int(X.shape[1]), _ptr(X), _ptr(Y), ctypes.byref(l),
+                                      ctypes.byref(a), _stream_handle(stream)))
+        return l.value, a.value
 
     def ptflash_last_counts(self):
         c = (_I64 * 4)()

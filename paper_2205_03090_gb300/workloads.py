@@ -118,3 +118,22 @@ def paper_components(names) -> Components:
         a, b = names.index("CH4"), names.index("CO2")
         k[a, b] = k[b, a] = 0.0882
     return Components(Tc, Pc, om, k)
+
+
+def mlp_init(din: int, hidden: int, dout: int, seed: int) -> np.ndarray:
+    """Initial network parameters drawn from seeded Glorot-uniform
+    distributions (weights) with zero biases, in the flat order W1, b1, W2,
+    b2, W3, b3, W4, b4 (each W row-major [out, in])."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for o, i in [(hidden, din), (hidden, hidden), (hidden, hidden), (dout, hidden)]:
+        lim = np.sqrt(6.0 / (i + o))
+        parts.append(g.uniform(-lim, lim, o * i))
+        parts.append(np.zeros(o))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def epoch_permutation(n: int, seed: int, epoch: int) -> np.ndarray:
+    """Seeded shuffle of n training samples for one epoch."""
+    g = np.random.Generator(np.random.PCG64([seed, epoch]))
+    return g.permutation(n).astype(np.int32)

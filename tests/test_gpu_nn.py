@@ -1,0 +1,125 @@
+"""Learned form (Sec. 4) on the GPU, through the C ABI.
+
+* One training step's gradient (the project's own forward / backward
+  kernels, BF16 weights and activations, FP32 sums) against the FP64
+  oracle of the same network on the same BF16 features and weights.
+* A short training run on plain-method flashes reduces the loss, and the
+  gated flash (classifier + initializer, p_l = 0.02, p_r = 0.98) matches the
+  CPU oracle of the plain method -- labels exact wherever |tpd| > 1e-8 up to
+  0.2 % classifier errors, two-phase values within 1e-8 up to 0.5 % of
+  multiple-stationary-point cases -- while running stability analysis on
+  far fewer mixtures.
+"""
+import numpy as np
+import pytest
+
+from paper_2205_03090_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ptf():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2205_03090_gb300 import build, ptflash
+    build.build()
+    ptflash.load()
+    return ptflash
+
+
+def _gpu_gradient(ptf, fl, which, hidden, theta, X, Y, perm):
+    """Gradient of one step: Adam with beta1 = beta2 = 0 and lr = eps = 1e6
+    moves theta by -g |g| / (|g| + 1e6) * ... = -g to ~1e-6 relative."""
+    mean = np.zeros(fl.nc + 2, np.float32)
+    std = np.ones(fl.nc + 2, np.float32)
+    fl.ptflash_nn_set(which, hidden, theta, mean, std)
+    fl.ptflash_nn_train_steps(which, X, Y, perm, 1, perm.shape[0], np.array([1e6], np.float32), beta1=0.0,
+                              beta2=0.0, eps=1e6)
+    new = fl.ptflash_nn_get(which, theta.size)
+    return (theta.astype(np.float64) - new.astype(np.float64))
+
+
+@pytest.mark.parametrize("which,hidden", [(0, 64), (1, 128)])
+def test_train_step_gradient_matches_oracle(ptf, oracle_mod, which, hidden):
+    import torch
+    from oracle import mlp
+    comp, cond = wl.workload("nc10_2phase_1e6", 512)
+    nc = comp.nc
+    fl = ptf.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=4096)
+    rng = np.random.default_rng(5)
+    dout = 1 if which == 0 else nc
+    theta = wl.mlp_init(nc + 2, hidden, dout, 11 + which)
+    theta = (theta + rng.normal(0, 0.02, theta.shape)).astype(np.float32)
+    mean, std = (np.r_[cond.z.mean(1), cond.P.mean(), cond.T.mean()].astype(np.float32),
+                 np.r_[cond.z.std(1), cond.P.std(), cond.T.std()].astype(np.float32))
+    fl.ptflash_nn_set(which, hidden, theta, mean, std)
+    P, T, z = (torch.tensor(a, device="cuda") for a in (cond.P, cond.T, cond.z))
+    X = torch.empty(nc + 2, 512, dtype=torch.float32, device="cuda")
+    fl.ptflash_nn_features(which, P, T, z.contiguous(), X)
+    if which == 0:
+        Y = torch.tensor((rng.uniform(size=512) < 0.4).astype(np.float32), device="cuda")[None, :]
+    else:
+        Y = torch.tensor(rng.normal(0, 1.0, (nc, 512)).astype(np.float32), device="cuda")
+    perm = torch.arange(512, dtype=torch.int32, device="cuda")
+    g = _gpu_gradient(ptf, fl, which, hidden, theta, X, Y, perm)
+    u = X.cpu().numpy().T.astype(np.float64)  # already the bf16 features
+    yt = Y.cpu().numpy().astype(np.float64)
+    yt = yt[0] if which == 0 else yt.T
+    _, ref = mlp.loss_and_grad(theta.astype(np.float64), u, yt, nc + 2, hidden, dout, "bce" if which == 0 else "mae")
+    # compare per parameter block (FP32 sums over 512 samples, BF16 operands)
+    k = 0
+    for o, i in mlp.layer_sizes(nc + 2, hidden, dout):
+        for size in (o * i, o):
+            a, b = g[k:k + size], ref[k:k + size]
+            scale = max(np.abs(b).max(), 1e-6)
+            assert np.abs(a - b).max() <= 2e-2 * scale, (which, k, np.abs(a - b).max(), scale)
+            k += size
+    fl.close()
+
+
+def test_training_and_learned_flash_parity(ptf, oracle_mod):
+    import torch
+    from paper_2205_03090_gb300 import nn
+    comp = wl.pseudo_components(10, 0)
+    w = wl.WORKLOADS["nc10_2phase_1e6"]
+    train_cond = wl.conditions(10, 200_000, 777, w["T_range"], w["P_range"], w["alpha"])
+    test_cond = wl.conditions(10, 20_000, 778, w["T_range"], w["P_range"], w["alpha"])
+    fl = ptf.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=1 << 18)
+    cfg = nn.TrainConfig(epochs=8, patience=8)
+    logs = nn.train_both(fl, train_cond, cfg)
+    c = logs[nn.CLASSIFIER].epochs
+    i = logs[nn.INITIALIZER].epochs
+    assert c[-1][2] < c[0][2] and i[-1][2] < i[0][2]  # validation loss fell
+    assert logs[nn.CLASSIFIER].test_acc > 0.97
+    P, T, z = (torch.tensor(a, device="cuda") for a in (test_cond.P, test_cond.T, test_cond.z))
+    z = z.contiguous()
+    plain = fl.ptflash_flash(P, T, z)
+    torch.cuda.synchronize()
+    plain_counts = fl.ptflash_last_counts()
+    learned = fl.ptflash_flash(P, T, z, use_nn=True)
+    torch.cuda.synchronize()
+    nn_counts = fl.ptflash_last_counts()
+    s = oracle_mod.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
+    o = oracle_mod.flash(s, test_cond.P, test_cond.T, test_cond.z)
+    g = {k: getattr(learned, k).cpu().numpy() for k in ("nphase", "beta", "x", "y", "status")}
+    lab = g["nphase"] != o["nphase"]
+    if lab.any():
+        tp = oracle_mod.tpd_min(s, test_cond.P[lab], test_cond.T[lab], np.ascontiguousarray(test_cond.z[:, lab]))
+        graded_bad = int((np.abs(tp) > 1e-8).sum())
+    else:
+        graded_bad = 0
+    both = (g["nphase"] == 2) & (o["nphase"] == 2)
+    db = np.abs(g["beta"] - o["beta"])[both]
+    dx = np.abs(g["x"] - o["x"]).max(0)[both]
+    print("learned: label mismatches", int(lab.sum()), "graded", graded_bad, "max dbeta", db.max(), "counts",
+          nn_counts, "plain", plain_counts)
+    # classifier errors beyond the confidence thresholds are rare; splits
+    # started from the initializer's K can reach another stationary point of
+    # G where several exist (half of them below the plain method's G), so a
+    # small fraction of two-phase values may differ after this short training
+    assert graded_bad <= 0.002 * test_cond.n
+    assert (db > 1e-8).mean() < 5e-3 and (dx > 1e-8).mean() < 5e-3
+    # the classifier skips stability analysis for most mixtures
+    assert nn_counts["stab"] < 0.2 * plain_counts["stab"]
+    fl.close()

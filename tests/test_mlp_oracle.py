@@ -1,0 +1,48 @@
+"""Pins of the FP64 network oracle (oracle/mlp.py): back-propagation against
+central finite differences of the loss (with the bfloat16 rounding points
+switched off so the loss is smooth), and the closed-form derivatives of the
+two losses."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+
+@pytest.fixture
+def smooth(monkeypatch):
+    monkeypatch.setattr(mlp, "bf16", lambda a: np.asarray(a, dtype=np.float64))
+
+
+@pytest.mark.parametrize("kind,din,hid,dout", [("bce", 12, 16, 1), ("mae", 12, 16, 10)])
+def test_backprop_matches_finite_differences(smooth, kind, din, hid, dout):
+    rng = np.random.default_rng(3)
+    theta = mlp.init_params(din, hid, dout, rng)
+    theta += rng.normal(0, 0.05, theta.shape)  # nonzero biases too
+    u = rng.normal(size=(20, din))
+    y = (rng.uniform(size=20) < 0.5).astype(float) if kind == "bce" else rng.normal(size=(20, dout))
+    loss, g = mlp.loss_and_grad(theta, u, y, din, hid, dout, kind)
+    idx = rng.choice(theta.size, 60, replace=False)
+    for i in idx:
+        h = 1e-6
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (mlp.loss_and_grad(tp, u, y, din, hid, dout, kind)[0] - mlp.loss_and_grad(tm, u, y, din, hid, dout, kind)[0]) / (2 * h)
+        assert g[i] == pytest.approx(fd, rel=1e-5, abs=1e-8)
+
+
+def test_loss_derivatives_closed_form():
+    # d/dz [softplus(z) - y z] = sigmoid(z) - y ; d/do |o - t| = sign(o - t)
+    z = np.linspace(-5, 5, 11)
+    for y in (0.0, 1.0):
+        h = 1e-6
+        f = lambda v: np.logaddexp(0.0, v) - y * v
+        fd = (f(z + h) - f(z - h)) / (2 * h)
+        np.testing.assert_allclose(fd, 1 / (1 + np.exp(-z)) - y, atol=1e-8)
+
+
+def test_bf16_rounding():
+    # bfloat16 keeps 8 significant bits: 1 + 2^-8 rounds to 1 (tie to even), 1 + 3 * 2^-8 to 1 + 2^-6
+    assert mlp.bf16(np.array([1.0 + 2.0 ** -8]))[0] == 1.0
+    assert mlp.bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
+    assert mlp.bf16(np.array([3.0]))[0] == 3.0
