@@ -375,17 +375,23 @@ __device__ __forceinline__ bool rachford_rice(const double* z, const double* K, 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
-// Cholesky of (H + eta diag(1)) in the scaled space; returns false if not PD.
+// Cholesky of (H + eta diag(1)) in the scaled space; returns -1 if positive
+// definite, else the column j whose pivot d_j <= 0 (in *dfail).  Lf holds L
+// below the diagonal and 1 / L_jj on it, so that the triangular solves
+// multiply instead of divide (FP64 division costs ~7 FMA slots here).
 template <int NC>
-__device__ __forceinline__ bool cholesky(const double* H, double eta, double* Lf) {
+__device__ __forceinline__ int cholesky(const double* H, double eta, double* Lf, double* dfail) {
 #pragma unroll 1
     for (int j = 0; j < NC; j++) {
         double d = H[tri(j, j)] + eta;
 #pragma unroll 1
         for (int k = 0; k < j; k++) d = fma(-Lf[tri(j, k)], Lf[tri(j, k)], d);
-        if (!(d > 0.0)) return false;
-        double ljj = sqrt(d), inv = 1.0 / ljj;
-        Lf[tri(j, j)] = ljj;
+        if (!(d > 0.0)) {
+            *dfail = d;
+            return j;
+        }
+        const double inv = rsqrt(d);
+        Lf[tri(j, j)] = inv;
 #pragma unroll 1
         for (int i = j + 1; i < NC; i++) {
             double s = H[tri(i, j)];
@@ -394,7 +400,26 @@ __device__ __forceinline__ bool cholesky(const double* H, double eta, double* Lf
             Lf[tri(i, j)] = s * inv;
         }
     }
-    return true;
+    return -1;
+}
+
+// After a factorisation of H + eta I failed at column j with pivot d <= 0:
+// w = (-L1^{-T} l, 1, 0, ...), with L1 the leading j x j factor and l the
+// computed part of row j, has w.(H + eta I).w = d, so the smallest eigenvalue
+// of H is at most d / ||w||^2 - eta (More and Sorensen 1983, Sec. 3).
+// Returns that bound on -lambda_min: eta - d / ||w||^2.
+template <int NC>
+__device__ __forceinline__ double shift_bound(const double* Lf, int j, double d, double eta) {
+    double w[NC], wn = 1.0;
+#pragma unroll 1
+    for (int i = j - 1; i >= 0; i--) {
+        double s = -Lf[tri(j, i)];
+#pragma unroll 1
+        for (int k = i + 1; k < j; k++) s = fma(-Lf[tri(k, i)], w[k], s);
+        w[i] = s * Lf[tri(i, i)];
+        wn = fma(w[i], w[i], wn);
+    }
+    return eta - d / wn;
 }
 
 // Solve L y = b (forward) in place
@@ -405,7 +430,7 @@ __device__ __forceinline__ void fwd(const double* Lf, double* b) {
         double s = b[i];
 #pragma unroll 1
         for (int k = 0; k < i; k++) s = fma(-Lf[tri(i, k)], b[k], s);
-        b[i] = s / Lf[tri(i, i)];
+        b[i] = s * Lf[tri(i, i)];
     }
 }
 
@@ -417,78 +442,133 @@ __device__ __forceinline__ void bwd(const double* Lf, double* b) {
         double s = b[i];
 #pragma unroll 1
         for (int k = i + 1; k < NC; k++) s = fma(-Lf[tri(k, i)], b[k], s);
-        b[i] = s / Lf[tri(i, i)];
+        b[i] = s * Lf[tri(i, i)];
     }
 }
 
-// Newton step d = -H^{-1} g in the scaled space (H already scaled).  Returns
-// false if H is not positive definite.
-template <int NC>
-__device__ __forceinline__ bool newton_scaled(const double* Hs, const double* gs, double* Lf, double* d) {
-    if (!cholesky<NC>(Hs, 0.0, Lf)) return false;
-    for (int i = 0; i < NC; i++) d[i] = -gs[i];
-    fwd<NC>(Lf, d);
-    bwd<NC>(Lf, d);
-    return true;
-}
+// Trust-region subproblem (Appendix B): minimise gs.u + u.Hs.u/2 subject to
+// ||u|| <= radius in the scaled space, by Hebden's iteration on the shift eta
+// of (Hs + eta I) u = -gs (Hebden 1973; More and Sorensen 1983), solved to
+// 1e-10 relative on ||u||.
+//
+// One call does one factorisation, so a persistent kernel spends one
+// factorisation per lane per trip and a lane that needs many shifts does not
+// hold its warp-mates inside a loop:
+//  - a fresh solve factors at eta = 0 and takes the Newton step when H is
+//    positive definite and the step fits;
+//  - otherwise it brackets the shift [elo, ehi] (Gershgorin and ||g|| / radius)
+//    and each further call takes one Newton step on 1/||u(eta)|| - 1/radius.
+//    A failed factorisation raises elo to its pivot's eigenvalue bound; a
+//    failure or a step that leaves the bracket continues from the safeguarded
+//    geometric midpoint max(sqrt(elo ehi), elo + 1e-3 (ehi - elo)) (More and
+//    Sorensen 1983, Sec. 3).  After kTRShiftCap calls the next positive
+//    definite factorisation ends the solve, so a solve takes at most
+//    kTRShiftCap + 2 calls.
+//    From the left of the solution these steps never overshoot (the function
+//    is concave), so the first starts from the eta = 0 factorisation, and a
+//    caller that shrank the radius around the same H passes the previous shift
+//    as a further lower bound.
+//  - the iteration also stops once the bracket has closed to 1e-12 relative:
+//    with the shift at the pole -lambda_min (the nearly hard case) ||u|| can
+//    change by 1e-8 relative for the smallest change of eta.
+// A radius <= 0 is not yet set: it becomes ||Newton step|| when H is positive
+// definite, else 1.  Returns 1 with the step in u (the shift used in sh.eta),
+// 0 if the iteration continues on the next call, and -1 with newton_only when
+// H is not positive definite.
+constexpr double kTRShiftTol = 1e-10;
+constexpr int kTRShiftCap = 40;
 
-// Trust-region subproblem (Appendix B) in the scaled space: minimise
-// gs.u + u.Hs.u/2 subject to ||u|| <= radius.  Hebden / More-Sorensen Newton
-// iteration on 1/||u(eta)|| - 1/radius with Cholesky factorisations,
-// safeguarded by a bracket [elo, ehi]; solved to 1e-10 relative on ||u||.
+struct TRShift {
+    double eta, elo, ehi;
+    int active, it;
+};
+
 template <int NC>
-__device__ __forceinline__ void tr_step_scaled(const double* Hs, const double* gs, double radius, double* Lf, double* u) {
-    double gn = 0.0, hn1 = 0.0, mind = 1e300;
-    for (int i = 0; i < NC; i++) {
-        gn = fma(gs[i], gs[i], gn);
-        double rs = 0.0;
-        for (int j = 0; j < NC; j++) rs += fabs(Hs[i >= j ? tri(i, j) : tri(j, i)]);
-        hn1 = fmax(hn1, rs);
-        mind = fmin(mind, Hs[tri(i, i)]);
-    }
-    gn = sqrt(gn);
-    double elo = fmax(0.0, fmax(-mind, gn / radius - hn1));
-    double ehi = gn / radius + hn1;
-    // eta = 0 first: the Newton step when it fits
-    double eta = 0.0;
-    if (cholesky<NC>(Hs, 0.0, Lf)) {
+__device__ __forceinline__ int tr_shift_step(const double* Hs, const double* gs, double& radius, double eta_lo,
+                                             bool newton_only, TRShift& sh, double* Lf, double* u) {
+    const double eta = sh.active ? sh.eta : 0.0;
+    double dfail = 0.0;
+    const int jf = cholesky<NC>(Hs, eta, Lf, &dfail);
+    const bool pd = jf < 0;
+    double un = 0.0;
+    if (pd) {
+#pragma unroll
         for (int i = 0; i < NC; i++) u[i] = -gs[i];
         fwd<NC>(Lf, u);
         bwd<NC>(Lf, u);
-        double un = 0.0;
-        for (int i = 0; i < NC; i++) un = fma(u[i], u[i], un);
-        if (sqrt(un) <= radius) return;
-        elo = fmax(elo, 0.0);
-        eta = fmax(elo, 1e-300);
-    } else {
-        eta = fmax(elo, 1e-12 * fmax(1.0, hn1));
-    }
-#pragma unroll 1
-    for (int it = 0; it < 100; it++) {
-        if (!cholesky<NC>(Hs, eta, Lf)) {
-            elo = eta;
-            eta = fmax(0.5 * (elo + ehi), 1.0001 * elo + 1e-300);
-            continue;
-        }
-        for (int i = 0; i < NC; i++) u[i] = -gs[i];
-        fwd<NC>(Lf, u);
-        bwd<NC>(Lf, u);
-        double un = 0.0;
+        if (newton_only) return 1;
+#pragma unroll
         for (int i = 0; i < NC; i++) un = fma(u[i], u[i], un);
         un = sqrt(un);
-        if (fabs(un - radius) <= 1e-10 * radius) return;
-        if (un < radius) ehi = eta; else elo = eta;
-        // q = L^{-1} u ; Newton update of the secular equation
-        double q[NC];
-        for (int i = 0; i < NC; i++) q[i] = u[i];
-        fwd<NC>(Lf, q);
-        double qn = 0.0;
-        for (int i = 0; i < NC; i++) qn = fma(q[i], q[i], qn);
-        double en = eta + (un * un / qn) * (un - radius) / radius;
-        if (!(en > elo && en < ehi)) en = 0.5 * (elo + ehi);
-        if (en == eta) return;
-        eta = en;
+        if (!sh.active) {
+            if (radius <= 0.0) radius = un;
+            if (un <= radius) {
+                sh.eta = 0.0;
+                return 1;
+            }
+        } else if (fabs(un - radius) <= kTRShiftTol * radius || sh.it >= kTRShiftCap) {
+            sh.active = 0;
+            return 1;
+        }
+    } else if (newton_only) {
+        return -1;
     }
+    if (!sh.active) {
+        if (radius <= 0.0) radius = 1.0;
+        double gn = 0.0, hn1 = 0.0, mind = 1e300;
+#pragma unroll 1
+        for (int i = 0; i < NC; i++) {
+            gn = fma(gs[i], gs[i], gn);
+            double rs = 0.0;
+#pragma unroll 1
+            for (int j = 0; j < NC; j++) rs += fabs(Hs[i >= j ? tri(i, j) : tri(j, i)]);
+            hn1 = fmax(hn1, rs);
+            mind = fmin(mind, Hs[tri(i, i)]);
+        }
+        gn = sqrt(gn);
+        sh.elo = fmax(fmax(0.0, eta_lo), fmax(-mind, gn / radius - hn1));
+        sh.ehi = gn / radius + hn1;
+        sh.active = 1;
+        sh.it = 0;
+    }
+    sh.it++;
+    if (!pd) {
+        // eigenvalue bound from the failed pivot, then the safeguarded
+        // midpoint of the bracket; past the cap the upper end, where H + eta I
+        // is positive definite, so that the next call ends the solve
+        sh.elo = fmax(sh.elo, shift_bound<NC>(Lf, jf, dfail, eta));
+        if (!(sh.ehi > sh.elo)) sh.ehi = 2.0 * sh.elo + 1e-300;
+        sh.eta = sh.it >= kTRShiftCap ? sh.ehi
+                                      : fmax(sqrt(fmax(sh.elo, 1e-300) * sh.ehi), sh.elo + 1e-3 * (sh.ehi - sh.elo));
+        return 0;
+    }
+    if (!(sh.ehi > sh.elo)) sh.ehi = 2.0 * sh.elo + 1e-300;
+    // positive definite, ||u|| off the radius: Newton step on the secular equation
+    if (un < radius) sh.ehi = eta;
+    else sh.elo = fmax(sh.elo, eta);
+    if (sh.ehi - sh.elo <= 1e-12 * sh.ehi) {  // shift pinned at the pole: ||u|| is as close as it gets
+        sh.active = 0;
+        sh.eta = eta;
+        return 1;
+    }
+    double q[NC], qn = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) q[i] = u[i];
+    fwd<NC>(Lf, q);
+#pragma unroll
+    for (int i = 0; i < NC; i++) qn = fma(q[i], q[i], qn);
+    double en = eta + (un * un / qn) * (un - radius) / radius;
+    if (un > radius) en = fmax(en, sh.elo);
+    if (!(en >= sh.elo && en < sh.ehi)) {  // out of the bracket: geometric midpoint
+        en = fmax(sqrt(fmax(sh.elo, 1e-300) * sh.ehi), sh.elo + 1e-3 * (sh.ehi - sh.elo));
+    }
+    if (en == eta) {  // no representable progress: take this step
+        sh.active = 0;
+        sh.eta = eta;
+        return 1;
+    }
+    sh.eta = en;
+    return 0;
 }
 
 // DEM factor (Sec. 2.2.1): lambda = (dk.d1)/(d1.d1) once settled (previous

@@ -443,15 +443,18 @@ __device__ __forceinline__ bool stab_point(const Comp<NC>& cp, const Mix<NC>& mx
     return true;
 }
 
-// One step = one evaluation (EOS and d ln phi / dn) of one trial: the start
-// point, or the trial point of a trust-region iteration.
+// One step = one factorisation of the subproblem and, once its step is known,
+// one evaluation (EOS and d ln phi / dn) of the trial point; the start point
+// is evaluated on the first step.  The tests that end a run follow the
+// evaluation, so a lane that finishes takes a new item on the next trip.
 template <int NC>
 struct StabTR {
     int64_t m, item;
     int t, it, iters, phase;  // phase 0: evaluate the start point; 1: iterate
     int32_t fl;
     Mix<NC> mx;
-    double d[NC], beta[NC], radius;
+    double d[NC], beta[NC], radius, eta_lo;
+    TRShift sh;
     StabPt<NC> cur;
 
     __device__ __forceinline__ void begin(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t it_) {
@@ -468,6 +471,8 @@ struct StabTR {
         fl = ws.tflag[t * n + m];
         it = iters = phase = 0;
         radius = -1.0;
+        eta_lo = 0.0;
+        sh.active = 0;
     }
 
     __device__ __forceinline__ void store(const WS& ws, int maxiter, int nonfinite) {
@@ -486,25 +491,10 @@ struct StabTR {
 #pragma unroll
             for (int i = 0; i < NC; i++) nxt.lnW[i] = cur.lnW[i];
         } else {
-            if (cur.tm < -kEpsNeg || maxabs<NC>(cur.g) < kTolStab) {
-                store(ws, 0, 0);
-                return 1;
-            }
-            if (it == kTRStab) {
-                store(ws, 1, 0);
-                return 1;
-            }
             double Lf[NC * (NC + 1) / 2];
-            if (radius < 0.0) {
-                if (newton_scaled<NC>(cur.H, cur.g, Lf, u)) {
-                    double s2 = 0.0;
-                    for (int i = 0; i < NC; i++) s2 = fma(u[i], u[i], s2);
-                    radius = sqrt(s2);
-                } else {
-                    radius = 1.0;
-                }
-            }
-            tr_step_scaled<NC>(cur.H, cur.g, radius, Lf, u);
+            // one shift per trip: few stability solves need more than one, and
+            // those lanes skip this trip's evaluation instead of holding the warp
+            if (tr_shift_step<NC>(cur.H, cur.g, radius, eta_lo, false, sh, Lf, u) == 0) return 0;
             for (int i = 0; i < NC; i++) {
                 double hd = 0.0;
                 for (int j = 0; j < NC; j++) hd = fma(cur.H[i >= j ? tri(i, j) : tri(j, i)], u[j], hd);
@@ -523,18 +513,29 @@ struct StabTR {
 #pragma unroll
             for (int i = 0; i < NC; i++) beta[i] = 2.0 * exp(0.5 * cur.lnW[i]);
             phase = 1;
-            return 0;
-        }
-        const bool trusted = fabs(pred) > kPredTrust * (1.0 + fabs(cur.tm));
-        const double rho = !ok ? -1.0 : (trusted ? (nxt.tm - cur.tm) / pred : 0.5);
-        if (rho > 0.0) {
+        } else {
+            const bool trusted = fabs(pred) > kPredTrust * (1.0 + fabs(cur.tm));
+            const double rho = !ok ? -1.0 : (trusted ? (nxt.tm - cur.tm) / pred : 0.5);
+            if (rho > 0.0) {
 #pragma unroll
-            for (int i = 0; i < NC; i++) beta[i] = fabs(beta[i] + u[i]);
-            cur = nxt;
+                for (int i = 0; i < NC; i++) beta[i] = fabs(beta[i] + u[i]);
+                cur = nxt;
+                eta_lo = 0.0;
+            } else {
+                eta_lo = sh.eta;  // same H, smaller radius: the shift can only grow
+            }
+            if (rho <= 0.25) radius *= 0.5;
+            else if (rho >= 0.75) radius *= 2.0;
+            iters = ++it;
         }
-        if (rho <= 0.25) radius *= 0.5;
-        else if (rho >= 0.75) radius *= 2.0;
-        iters = ++it;
+        if (cur.tm < -kEpsNeg || maxabs<NC>(cur.g) < kTolStab) {
+            store(ws, 0, 0);
+            return 1;
+        }
+        if (it == kTRStab) {
+            store(ws, 1, 0);
+            return 1;
+        }
         return 0;
     }
 };
@@ -821,15 +822,19 @@ __device__ __forceinline__ double boundary_cut(const double* z, const double* nV
     return tau;
 }
 
-// One step = one evaluation of both phases with their derivatives: the start
-// point, a trust-region trial point, or a Newton-polish point.
+// One step = one factorisation of the subproblem and, once its step is known,
+// one evaluation of both phases with their derivatives at the trial point
+// (trust-region or Newton polish; the start point on the first step).  Both
+// kinds of step share the one factorisation site, and the tests that end a
+// run follow the evaluation.
 template <int NC>
 struct SplitTR {
     int64_t m;
     int it, iters, newton_steps, phase;  // phase 0: start point; 1: trust region; 2: Newton polish
     int32_t st;
     Mix<NC> mx;
-    double z[NC], nV[NC], radius;
+    double z[NC], nV[NC], radius, eta_lo;
+    TRShift sh;
     SplitPt<NC> cur;
 
     __device__ __forceinline__ void begin(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t mm) {
@@ -844,6 +849,8 @@ struct SplitTR {
         st = io.status[m];
         it = iters = newton_steps = phase = 0;
         radius = -1.0;
+        eta_lo = 0.0;
+        sh.active = 0;
     }
 
     __device__ __forceinline__ int finish(const IO& io, int kind) {  // kind 0 result, 1 non-finite
@@ -863,61 +870,42 @@ struct SplitTR {
 
     // 0 continue, 1 done
     __device__ __forceinline__ int step(const Comp<NC>& cp, const WS& ws, const IO& io) {
-        double Lf[NC * (NC + 1) / 2], u[NC], dstep[NC], trial[NC], pred = 0.0;
+        double u[NC], dstep[NC], trial[NC], pred = 0.0;
         if (phase == 0) {
 #pragma unroll
             for (int i = 0; i < NC; i++) trial[i] = nV[i];
         } else {
-            const double res = maxabs<NC>(cur.gt);
-            if (phase == 1 && res < kTolSplitTR) phase = 2;
-            if (phase == 2) {
-                if (res <= kTolFug && newton_steps >= 1) return finish(io, 0);
-                if (newton_steps == kNewtonPolish) {
-                    st |= ST_MAXITER;
-                    return finish(io, 0);
-                }
-                if (!newton_scaled<NC>(cur.Hs, cur.gs, Lf, u)) {
-                    if (res > kTolFug) st |= ST_MAXITER;
-                    return finish(io, 0);
-                }
+            double Lf[NC * (NC + 1) / 2];
+            // split solves need several shifts where they need any, so they
+            // finish within the trip (one factorisation site all the same)
+            int r = 0;
+#pragma unroll 1
+            for (int k = 0; k < kTRShiftCap + 2 && r == 0; k++)
+                r = tr_shift_step<NC>(cur.Hs, cur.gs, radius, eta_lo, phase == 2, sh, Lf, u);
+            if (r == 0) return 0;
+            if (r < 0) {  // Newton polish on an indefinite Hessian: stop here
+                if (maxabs<NC>(cur.gt) > kTolFug) st |= ST_MAXITER;
+                return finish(io, 0);
+            }
 #pragma unroll
-                for (int i = 0; i < NC; i++) dstep[i] = cur.S[i] * u[i];
-                const double tau = boundary_cut<NC>(z, nV, dstep);
+            for (int i = 0; i < NC; i++) dstep[i] = cur.S[i] * u[i];
+            const double tau = boundary_cut<NC>(z, nV, dstep);
+            if (tau < 1.0) {
 #pragma unroll
-                for (int i = 0; i < NC; i++) trial[i] = nV[i] + tau * dstep[i];
-            } else {
-                if (it == kTRSplit) {
-                    st |= ST_MAXITER;
-                    return finish(io, 0);
+                for (int i = 0; i < NC; i++) {
+                    u[i] *= tau;
+                    dstep[i] *= tau;
                 }
-                if (radius < 0.0) {
-                    if (newton_scaled<NC>(cur.Hs, cur.gs, Lf, u)) {
-                        double s2 = 0.0;
-                        for (int i = 0; i < NC; i++) s2 = fma(u[i], u[i], s2);
-                        radius = sqrt(s2);
-                    } else {
-                        radius = 1.0;
-                    }
-                }
-                tr_step_scaled<NC>(cur.Hs, cur.gs, radius, Lf, u);
-#pragma unroll
-                for (int i = 0; i < NC; i++) dstep[i] = cur.S[i] * u[i];
-                const double tau = boundary_cut<NC>(z, nV, dstep);
-                if (tau < 1.0) {
-#pragma unroll
-                    for (int i = 0; i < NC; i++) {
-                        u[i] *= tau;
-                        dstep[i] *= tau;
-                    }
-                }
+            }
+            if (phase == 1) {
                 for (int i = 0; i < NC; i++) {
                     double hd = 0.0;
                     for (int j = 0; j < NC; j++) hd = fma(cur.Hs[i >= j ? tri(i, j) : tri(j, i)], u[j], hd);
                     pred = fma(cur.gs[i], u[i], fma(0.5 * u[i], hd, pred));
                 }
-#pragma unroll
-                for (int i = 0; i < NC; i++) trial[i] = nV[i] + dstep[i];
             }
+#pragma unroll
+            for (int i = 0; i < NC; i++) trial[i] = nV[i] + dstep[i];
         }
         SplitPt<NC> nxt;
         const bool ok = split_point<NC>(cp, mx, z, trial, nxt);
@@ -925,27 +913,40 @@ struct SplitTR {
             if (!ok) return finish(io, 1);
             cur = nxt;
             phase = 1;
-            return 0;
-        }
-        if (phase == 2) {  // Newton polish steps are taken unconditionally
+        } else if (phase == 2) {  // Newton polish steps are taken unconditionally
             if (!ok) return finish(io, 1);
 #pragma unroll
             for (int i = 0; i < NC; i++) nV[i] = trial[i];
             cur = nxt;
             newton_steps++;
             iters++;
-            return 0;
-        }
-        const bool trusted = fabs(pred) > kPredTrust * (1.0 + fabs(cur.G));
-        const double rho = !ok ? -1.0 : (trusted ? (nxt.G - cur.G) / pred : 0.5);
-        if (rho > 0.0) {
+        } else {
+            const bool trusted = fabs(pred) > kPredTrust * (1.0 + fabs(cur.G));
+            const double rho = !ok ? -1.0 : (trusted ? (nxt.G - cur.G) / pred : 0.5);
+            if (rho > 0.0) {
 #pragma unroll
-            for (int i = 0; i < NC; i++) nV[i] = trial[i];
-            cur = nxt;
+                for (int i = 0; i < NC; i++) nV[i] = trial[i];
+                cur = nxt;
+                eta_lo = 0.0;
+            } else {
+                eta_lo = sh.eta;  // same H, smaller radius: the shift can only grow
+            }
+            if (rho <= 0.25) radius *= 0.5;
+            else if (rho >= 0.75) radius *= 2.0;
+            iters = ++it;
         }
-        if (rho <= 0.25) radius *= 0.5;
-        else if (rho >= 0.75) radius *= 2.0;
-        iters = ++it;
+        const double res = maxabs<NC>(cur.gt);
+        if (phase == 1 && res < kTolSplitTR) phase = 2;
+        if (phase == 2) {
+            if (res <= kTolFug && newton_steps >= 1) return finish(io, 0);
+            if (newton_steps == kNewtonPolish) {
+                st |= ST_MAXITER;
+                return finish(io, 0);
+            }
+        } else if (it == kTRSplit) {
+            st |= ST_MAXITER;
+            return finish(io, 0);
+        }
         return 0;
     }
 };
