@@ -366,7 +366,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-sample", type=int, default=100_000)
+    ap.add_argument("--cpu-sample", type=int, default=500_000)
     ap.add_argument("--ref-sample", type=int, default=20_000)
     ap.add_argument("--n", type=int, default=0, help="mixtures per rank (default: the workload's 1e6)")
     ap.add_argument("--learned-n", type=int, default=10_000_000,
