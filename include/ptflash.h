@@ -172,6 +172,54 @@ int ptflash_flash_noalloc(int nc, const double* Tc, const double* Pc, const doub
                           void* stream);
 
 /*
+ * Uneven batches: many fluid systems, each with its own number of components
+ * (2..16), component data and mixtures, flashed by one CUDA graph launch.  The
+ * paper flashes batches of one fluid system (Sec. 3); a batch of systems is
+ * the same plain method (Sec. 2.2.3) per mixture, with each mixture's own
+ * component data.  Results equal ptflash_flash's for each system.
+ *
+ * ptflash_batch_create: HOST arrays.  nsys systems; system s has nc[s]
+ *   components and n[s] >= 0 mixtures.  Tc, Pc, omega are packed by system
+ *   (system s's components start at sum_{r<s} nc[r]); kij is packed by system
+ *   (system s's nc[s] x nc[s] row-major, symmetric, zero-diagonal block starts
+ *   at sum_{r<s} nc[r]^2).  Validates the data like ptflash_set_components,
+ *   allocates every device buffer of the batch (component tables; per nc a
+ *   workspace, staging of (4 nc + 3) doubles + 10 ints per mixture, a stream)
+ *   and synchronises.  Returns PTF_ERR_UNSUPPORTED for nc outside [2, 16],
+ *   PTF_ERR_NO_MEMORY if an allocation fails.
+ * ptflash_batch_flash: DEVICE arrays packed like the systems: P, T, nphase,
+ *   beta, status, iters (optional, may be NULL) hold N = sum n[s] entries,
+ *   system s's mixtures from off[s] = sum_{r<s} n[r]; z, x, y, K hold system s's
+ *   component-major [nc[s]][n[s]] block from zoff[s] = sum_{r<s} nc[r] n[r].
+ *   One graph launch on `stream`: the systems are grouped by nc, and each
+ *   group (its own stream branch of the graph) gathers its mixtures into a
+ *   contiguous slice, runs the flash pipeline with per-mixture component
+ *   tables and scatters the results.  The graph is captured on the first call
+ *   and again whenever a pointer argument differs from the previous call's;
+ *   calls on one batch must be ordered on one stream.
+ * ptflash_batch_tune: times each nc group alone (synchronously, twice per
+ *   candidate) with its persistent kernels at the device-filling default or
+ *   at 1, 2, 3 or 4 resident 128-thread blocks per SM, keeps the fastest and
+ *   drops the captured graph.  HOST blocks_per_sm[17] (optional) gets the
+ *   choice per nc (0 = default, also for absent nc), HOST group_ms[17]
+ *   (optional) its time.  Same array arguments as ptflash_batch_flash, whose
+ *   outputs it overwrites.
+ * ptflash_batch_info: number of nc groups, nodes of the captured graph (0
+ *   before the first flash), total mixtures; any pointer may be NULL.
+ */
+typedef struct ptflash_batch ptflash_batch;
+int ptflash_batch_create(ptflash_batch** out, int nsys, const int32_t* nc, const int64_t* n, const double* Tc,
+                         const double* Pc, const double* omega, const double* kij);
+int ptflash_batch_destroy(ptflash_batch* b);
+int ptflash_batch_flash(ptflash_batch* b, const double* P, const double* T, const double* z, int32_t* nphase,
+                        double* beta, double* x, double* y, double* K, int32_t* status, int32_t* iters,
+                        void* stream);
+int ptflash_batch_tune(ptflash_batch* b, const double* P, const double* T, const double* z, int32_t* nphase,
+                       double* beta, double* x, double* y, double* K, int32_t* status, int32_t* iters,
+                       int32_t* blocks_per_sm, float* group_ms);
+int ptflash_batch_info(const ptflash_batch* b, int32_t* ngroups, int64_t* graph_nodes, int64_t* mixtures);
+
+/*
  * Learned form (Sec. 4 of the paper).  which = 0: stability classifier
  * (3 hidden layers of `hidden` SiLU units, one logit; p = sigmoid(logit) is
  * the probability that the mixture is stable); which = 1: ln K initializer

@@ -49,6 +49,8 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     srcs = _sources()
     objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
     todo = [(s, o) for s, o in zip(srcs, objs) if _stale(o, s)]
+    # the per-nc instantiation units take longer the larger nc: start those first
+    todo.sort(key=lambda so: -int(os.path.basename(so[0])[9:11]) if "ptf_inst_" in so[0] else 0)
 
     def compile_one(so):
         s, o = so

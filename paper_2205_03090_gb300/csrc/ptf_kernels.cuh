@@ -48,6 +48,22 @@ struct IO {
 enum { Q_STAB = 0, Q_SPLIT = 1, Q_STAB_TR = 2, Q_SPLIT_TR = 3 };
 enum { H_PRE = 8, H_STAB = 9, H_STAB_TR = 10, H_SPLIT = 11, H_SPLIT_TR = 12 };
 
+// Component data of a launch.  OneSys: one fluid system, a kernel parameter
+// read through the constant bank.  ManySys: several systems of the same nc (a
+// batch of uneven systems is grouped by nc), a table in global memory and the
+// system of each mixture.
+template <int NC>
+struct OneSys {
+    Comp<NC> c;
+    __device__ __forceinline__ const Comp<NC>& of(int64_t) const { return c; }
+};
+template <int NC>
+struct ManySys {
+    const Comp<NC>* tab;  // [number of systems]
+    const int32_t* sys;   // [n]: system of each mixture
+    __device__ __forceinline__ const Comp<NC>& of(int64_t m) const { return tab[__ldg(sys + m)]; }
+};
+
 // Warp-aggregated append: every lane of the warp must call it (full mask).
 __device__ __forceinline__ void warp_append(int32_t* cnt, int32_t* queue, bool pred, int32_t value) {
     const unsigned m = __ballot_sync(0xffffffffu, pred);
@@ -129,8 +145,9 @@ __device__ __forceinline__ void write_two(const IO& io, int64_t m, double th, co
 // outputs here; the stability-only pipeline enqueues every other mixture.
 // ---------------------------------------------------------------------------
 // Returns 0 done (non-finite), 1 to the stability queue, 2 to the precheck.
-template <int NC, bool PRECHECK>
-__device__ __forceinline__ int prep_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t m) {
+template <int NC, bool PRECHECK, class CS>
+__device__ __forceinline__ int prep_item(const CS& cs, const WS& ws, const IO& io, int64_t m) {
+    const Comp<NC>& cp = cs.of(m);
     const int64_t n = ws.n;
     const double P = io.P[m], T = io.T[m];
     double z[NC];
@@ -172,10 +189,10 @@ __device__ __forceinline__ int prep_item(const Comp<NC>& cp, const WS& ws, const
     return 2;
 }
 
-template <int NC, bool PRECHECK>
-__global__ void __launch_bounds__(128) k_prep(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+template <int NC, bool PRECHECK, class CS>
+__global__ void __launch_bounds__(128) k_prep(const __grid_constant__ CS cs, WS ws, IO io) {
     PTF_WARP_ROUNDS(ws.n, m, valid) {
-        const int route = valid ? prep_item<NC, PRECHECK>(cp, ws, io, m) : 0;
+        const int route = valid ? prep_item<NC, PRECHECK>(cs, ws, io, m) : 0;
         warp_append(ws.cnt + Q_STAB, ws.q_stab, route == 1, (int32_t)m);
     }
 }
@@ -191,8 +208,10 @@ struct PrecheckSS {
     double z[NC], lnK[NC], th;
     int it;
 
-    __device__ __forceinline__ void begin(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t mm) {
+    template <class CS>
+    __device__ __forceinline__ void begin(const CS& cs, const WS& ws, const IO& io, int64_t mm) {
         m = mm;
+        const Comp<NC>& cp = cs.of(m);
         load_mix<NC>(ws, m, mx);
 #pragma unroll
         for (int i = 0; i < NC; i++) z[i] = io.z[i * io.ld + m];
@@ -202,7 +221,9 @@ struct PrecheckSS {
     }
 
     // 0 continue, 1 to the stability queue, 2 to the split queue
-    __device__ __forceinline__ int step(const Comp<NC>& cp, const WS& ws, const IO& io) {
+    template <class CS>
+    __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io) {
+        const Comp<NC>& cp = cs.of(m);
         const int64_t n = ws.n;
         double K[NC], t[NC], x[NC], y[NC];
         Phase<NC> pl, pv;
@@ -244,8 +265,8 @@ struct PrecheckSS {
 
 // Persistent kernel: lanes whose mixture finished take the next one, so the
 // warp keeps all lanes busy until the batch is exhausted.
-template <int NC>
-__global__ void __launch_bounds__(128) k_precheck(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+template <int NC, class CS>
+__global__ void __launch_bounds__(128) k_precheck(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = ws.n;
     PrecheckSS<NC> s;
     bool have = false, drained = false;
@@ -255,12 +276,12 @@ __global__ void __launch_bounds__(128) k_precheck(const __grid_constant__ Comp<N
             if (io.status[pos] & ST_NONFINITE) {
                 // already final; this lane fetches again next round
             } else {
-                s.begin(cp, ws, io, pos);
+                s.begin(cs, ws, io, pos);
                 have = true;
             }
         }
         if (!__any_sync(0xffffffffu, have) && drained) break;
-        const int r = have ? s.step(cp, ws, io) : 0;
+        const int r = have ? s.step(cs, ws, io) : 0;
         warp_append(ws.cnt + Q_STAB, ws.q_stab, r == 1, (int32_t)s.m);
         warp_append(ws.cnt + Q_SPLIT, ws.q_split, r == 2, (int32_t)s.m);
         if (r) have = false;
@@ -306,10 +327,12 @@ struct StabSS {
     int t, it, iters;
     bool dem_pending;
 
-    __device__ __forceinline__ void begin(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t it_) {
+    template <class CS>
+    __device__ __forceinline__ void begin(const CS& cs, const WS& ws, const IO& io, int64_t it_) {
         const int64_t n = ws.n;
         item = it_;
         m = ws.q_stab[item >> 1];
+        const Comp<NC>& cp = cs.of(m);
         t = (int)(item & 1);
         load_mix<NC>(ws, m, mx);
         double lnKw[NC];
@@ -342,7 +365,9 @@ struct StabSS {
     }
 
     // 0 continue, 1 done, 2 needs the trust region
-    __device__ __forceinline__ int step(const Comp<NC>& cp, const WS& ws, const IO& io) {
+    template <class CS>
+    __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io) {
+        const Comp<NC>& cp = cs.of(m);
         double W[NC], c[NC], gt[NC], Wt;
         Phase<NC> ph;
         const bool bad = !stab_eval<NC>(cp, mx, d, lnW, W, Wt, c, ph, gt, tm);
@@ -395,19 +420,19 @@ struct StabSS {
     }
 };
 
-template <int NC>
-__global__ void __launch_bounds__(128) k_stab_ss(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+template <int NC, class CS>
+__global__ void __launch_bounds__(128) k_stab_ss(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = 2 * (int64_t)(*(volatile int32_t*)(ws.cnt + Q_STAB));
     StabSS<NC> s;
     bool have = false, drained = false;
     for (;;) {
         const int64_t pos = warp_fetch(ws.cnt + H_STAB, !have, len, drained);
         if (pos >= 0) {
-            s.begin(cp, ws, io, pos);
+            s.begin(cs, ws, io, pos);
             have = true;
         }
         if (!__any_sync(0xffffffffu, have)) break;
-        const int r = have ? s.step(cp, ws, io) : 0;
+        const int r = have ? s.step(cs, ws, io) : 0;
         warp_append(ws.cnt + Q_STAB_TR, ws.q_stab_tr, r == 2, (int32_t)s.item);
         if (r) have = false;
     }
@@ -457,10 +482,12 @@ struct StabTR {
     TRShift sh;
     StabPt<NC> cur;
 
-    __device__ __forceinline__ void begin(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t it_) {
+    template <class CS>
+    __device__ __forceinline__ void begin(const CS& cs, const WS& ws, const IO& io, int64_t it_) {
         const int64_t n = ws.n;
         item = it_;
         m = ws.q_stab[item >> 1];
+        const Comp<NC>& cp = cs.of(m);
         t = (int)(item & 1);
         load_mix<NC>(ws, m, mx);
 #pragma unroll
@@ -484,7 +511,9 @@ struct StabTR {
     }
 
     // 0 continue, 1 done
-    __device__ __forceinline__ int step(const Comp<NC>& cp, const WS& ws, const IO& io) {
+    template <class CS>
+    __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io) {
+        const Comp<NC>& cp = cs.of(m);
         StabPt<NC> nxt;
         double u[NC], pred = 0.0;
         if (phase == 0) {
@@ -540,19 +569,19 @@ struct StabTR {
     }
 };
 
-template <int NC>
-__global__ void __launch_bounds__(128) k_stab_tr(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+template <int NC, class CS>
+__global__ void __launch_bounds__(128) k_stab_tr(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_STAB_TR);
     StabTR<NC> s;
     bool have = false, drained = false;
     for (;;) {
         const int64_t pos = warp_fetch(ws.cnt + H_STAB_TR, !have, len, drained);
         if (pos >= 0) {
-            s.begin(cp, ws, io, ws.q_stab_tr[pos]);
+            s.begin(cs, ws, io, ws.q_stab_tr[pos]);
             have = true;
         }
         if (!__any_sync(0xffffffffu, have)) break;
-        if (have && s.step(cp, ws, io)) have = false;
+        if (have && s.step(cs, ws, io)) have = false;
     }
 }
 
@@ -560,8 +589,9 @@ __global__ void __launch_bounds__(128) k_stab_tr(const __grid_constant__ Comp<NC
 // Stability decision and K re-estimate (Sec. 2.2.1, last sentence).
 // ---------------------------------------------------------------------------
 // Returns true if the mixture goes to the split queue.
-template <int NC>
-__device__ __forceinline__ bool stab_decide_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t m) {
+template <int NC, class CS>
+__device__ __forceinline__ bool stab_decide_item(const CS& cs, const WS& ws, const IO& io, int64_t m) {
+    const Comp<NC>& cp = cs.of(m);
     const int64_t n = ws.n;
     bool to_split = false;
     {
@@ -600,12 +630,12 @@ __device__ __forceinline__ bool stab_decide_item(const Comp<NC>& cp, const WS& w
     return to_split;
 }
 
-template <int NC>
-__global__ void __launch_bounds__(128) k_stab_decide(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+template <int NC, class CS>
+__global__ void __launch_bounds__(128) k_stab_decide(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_STAB);
     PTF_WARP_ROUNDS(len, qi, valid) {
         const int64_t m = valid ? ws.q_stab[qi] : 0;
-        const bool to_split = valid ? stab_decide_item<NC>(cp, ws, io, m) : false;
+        const bool to_split = valid ? stab_decide_item<NC>(cs, ws, io, m) : false;
         warp_append(ws.cnt + Q_SPLIT, ws.q_split, to_split, (int32_t)m);
     }
 }
@@ -622,9 +652,11 @@ struct SplitSS {
     int it, iters;
     bool dem_pending;
 
-    __device__ __forceinline__ void begin(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t mm) {
+    template <class CS>
+    __device__ __forceinline__ void begin(const CS& cs, const WS& ws, const IO& io, int64_t mm) {
         const int64_t n = ws.n;
         m = mm;
+        const Comp<NC>& cp = cs.of(m);
         load_mix<NC>(ws, m, mx);
 #pragma unroll
         for (int i = 0; i < NC; i++) {
@@ -645,7 +677,9 @@ struct SplitSS {
     }
 
     // 0 continue, 1 done, 2 needs the trust region
-    __device__ __forceinline__ int step(const Comp<NC>& cp, const WS& ws, const IO& io) {
+    template <class CS>
+    __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io) {
+        const Comp<NC>& cp = cs.of(m);
         const int64_t n = ws.n;
         double K[NC], t[NC], x[NC], y[NC], gt[NC];
         Phase<NC> pl, pv;
@@ -735,19 +769,19 @@ struct SplitSS {
     }
 };
 
-template <int NC>
-__global__ void __launch_bounds__(128) k_split_ss(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+template <int NC, class CS>
+__global__ void __launch_bounds__(128) k_split_ss(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_SPLIT);
     SplitSS<NC> s;
     bool have = false, drained = false;
     for (;;) {
         const int64_t pos = warp_fetch(ws.cnt + H_SPLIT, !have, len, drained);
         if (pos >= 0) {
-            s.begin(cp, ws, io, ws.q_split[pos]);
+            s.begin(cs, ws, io, ws.q_split[pos]);
             have = true;
         }
         if (!__any_sync(0xffffffffu, have)) break;
-        const int r = have ? s.step(cp, ws, io) : 0;
+        const int r = have ? s.step(cs, ws, io) : 0;
         warp_append(ws.cnt + Q_SPLIT_TR, ws.q_split_tr, r == 2, (int32_t)s.m);
         if (r) have = false;
     }
@@ -837,9 +871,11 @@ struct SplitTR {
     TRShift sh;
     SplitPt<NC> cur;
 
-    __device__ __forceinline__ void begin(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t mm) {
+    template <class CS>
+    __device__ __forceinline__ void begin(const CS& cs, const WS& ws, const IO& io, int64_t mm) {
         const int64_t n = ws.n;
         m = mm;
+        const Comp<NC>& cp = cs.of(m);
         load_mix<NC>(ws, m, mx);
 #pragma unroll
         for (int i = 0; i < NC; i++) {
@@ -869,7 +905,9 @@ struct SplitTR {
     }
 
     // 0 continue, 1 done
-    __device__ __forceinline__ int step(const Comp<NC>& cp, const WS& ws, const IO& io) {
+    template <class CS>
+    __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io) {
+        const Comp<NC>& cp = cs.of(m);
         double u[NC], dstep[NC], trial[NC], pred = 0.0;
         if (phase == 0) {
 #pragma unroll
@@ -951,19 +989,19 @@ struct SplitTR {
     }
 };
 
-template <int NC>
-__global__ void __launch_bounds__(128) k_split_tr(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+template <int NC, class CS>
+__global__ void __launch_bounds__(128) k_split_tr(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_SPLIT_TR);
     SplitTR<NC> s;
     bool have = false, drained = false;
     for (;;) {
         const int64_t pos = warp_fetch(ws.cnt + H_SPLIT_TR, !have, len, drained);
         if (pos >= 0) {
-            s.begin(cp, ws, io, ws.q_split_tr[pos]);
+            s.begin(cs, ws, io, ws.q_split_tr[pos]);
             have = true;
         }
         if (!__any_sync(0xffffffffu, have)) break;
-        if (have && s.step(cp, ws, io)) have = false;
+        if (have && s.step(cs, ws, io)) have = false;
     }
 }
 
@@ -971,8 +1009,9 @@ __global__ void __launch_bounds__(128) k_split_tr(const __grid_constant__ Comp<N
 // Stability-only outputs (ptflash_stability): io.nphase = stable flag,
 // io.beta = min tm, io.K = K re-estimate.
 // ---------------------------------------------------------------------------
-template <int NC>
-__device__ __forceinline__ void stab_out_item(const Comp<NC>& cp, const WS& ws, const IO& io, int64_t m) {
+template <int NC, class CS>
+__device__ __forceinline__ void stab_out_item(const CS& cs, const WS& ws, const IO& io, int64_t m) {
+    const Comp<NC>& cp = cs.of(m);
     const int64_t n = ws.n;
     {
         {
@@ -996,11 +1035,11 @@ __device__ __forceinline__ void stab_out_item(const Comp<NC>& cp, const WS& ws, 
     }
 }
 
-template <int NC>
-__global__ void __launch_bounds__(128) k_stab_out(const __grid_constant__ Comp<NC> cp, WS ws, IO io) {
+template <int NC, class CS>
+__global__ void __launch_bounds__(128) k_stab_out(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_STAB);
     PTF_WARP_ROUNDS(len, qi, valid) {
-        if (valid) stab_out_item<NC>(cp, ws, io, ws.q_stab[qi]);
+        if (valid) stab_out_item<NC>(cs, ws, io, ws.q_stab[qi]);
     }
 }
 
@@ -1011,8 +1050,8 @@ __global__ void __launch_bounds__(128) k_stab_out(const __grid_constant__ Comp<N
 // analysis with trials initialised from the initializer's K (Wilson K when
 // the initializer output is not finite).  ln K is clamped to [-15, 15].
 // ---------------------------------------------------------------------------
-template <int NC>
-__global__ void __launch_bounds__(128) k_nn_route(const __grid_constant__ Comp<NC> cp, WS ws, IO io, float p_l,
+template <int NC, class CS>
+__global__ void __launch_bounds__(128) k_nn_route(const __grid_constant__ CS cs, WS ws, IO io, float p_l,
                                                   float p_r) {
     const int64_t n = ws.n;
     PTF_WARP_ROUNDS(n, m, valid) {

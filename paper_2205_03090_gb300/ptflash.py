@@ -74,6 +74,16 @@ def load(path: str = LIB_PATH):
     for f in ("ptflash_nn_set", "ptflash_nn_get", "ptflash_nn_features", "ptflash_nn_infer", "ptflash_nn_train_steps",
               "ptflash_nn_eval"):
         getattr(lib, f).restype = ctypes.c_int
+    _I32P = ctypes.POINTER(ctypes.c_int32)
+    lib.ptflash_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, _I32P, ctypes.POINTER(_I64), _D, _D, _D,
+                                         _D]
+    lib.ptflash_batch_destroy.argtypes = [_VP]
+    lib.ptflash_batch_flash.argtypes = [_VP] + [_VP] * 10 + [_VP]
+    lib.ptflash_batch_tune.argtypes = [_VP] + [_VP] * 10 + [_I32P, ctypes.POINTER(ctypes.c_float)]
+    lib.ptflash_batch_info.argtypes = [_VP, _I32P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]
+    for f in ("ptflash_batch_create", "ptflash_batch_destroy", "ptflash_batch_flash", "ptflash_batch_tune",
+              "ptflash_batch_info"):
+        getattr(lib, f).restype = ctypes.c_int
     lib.ptflash_strerror.argtypes = [ctypes.c_int]
     lib.ptflash_strerror.restype = ctypes.c_char_p
     lib.ptflash_last_cuda_error.restype = ctypes.c_char_p
@@ -243,3 +253,88 @@ class Flash:
         c = (_I64 * 4)()
         _check(load().ptflash_last_counts(self._h, c))
         return dict(stab=c[0], split=c[1], stab_tr=c[2], split_tr=c[3])
+
+
+class Batch:
+    """An uneven batch of fluid systems (ptflash_batch_create).
+
+    systems: list of (Tc, Pc, omega, kij) per system; n: mixtures per system.
+    Mixture arrays are packed by system: P, T and the per-mixture outputs hold
+    sum(n) entries in system order; z, x, y, K are the concatenation of each
+    system's flattened component-major [nc_s, n_s] block."""
+
+    def __init__(self, systems, n):
+        lib = load()
+        self.nc = np.array([len(np.atleast_1d(s[0])) for s in systems], np.int32)
+        self.n = np.array(n, np.int64)
+        self.off = np.concatenate([[0], np.cumsum(self.n)]).astype(np.int64)
+        self.zoff = np.concatenate([[0], np.cumsum(self.nc.astype(np.int64) * self.n)]).astype(np.int64)
+        self.N = int(self.off[-1])
+        self.Z = int(self.zoff[-1])
+        cat = lambda k: np.ascontiguousarray(np.concatenate([np.ravel(np.asarray(s[k], np.float64)) for s in systems]))
+        Tc, Pc, om, kij = cat(0), cat(1), cat(2), cat(3)
+        h = _VP()
+        _check(lib.ptflash_batch_create(ctypes.byref(h), len(systems), self.nc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                        self.n.ctypes.data_as(ctypes.POINTER(_I64)), Tc.ctypes.data_as(_D),
+                                        Pc.ctypes.data_as(_D), om.ctypes.data_as(_D), kij.ctypes.data_as(_D)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ptflash_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack(self, parts, device="cuda"):
+        """Pack per-system (P, T, z[nc, n]) NumPy arrays into device tensors."""
+        import torch
+        P = torch.tensor(np.concatenate([p[0] for p in parts]), dtype=torch.float64, device=device)
+        T = torch.tensor(np.concatenate([p[1] for p in parts]), dtype=torch.float64, device=device)
+        z = torch.tensor(np.concatenate([np.ravel(p[2]) for p in parts]), dtype=torch.float64, device=device)
+        return P, T, z
+
+    def alloc_outputs(self, device="cuda"):
+        import torch
+        f64 = dict(dtype=torch.float64, device=device)
+        i32 = dict(dtype=torch.int32, device=device)
+        return FlashResult(torch.empty(self.N, **i32), torch.empty(self.N, **f64), torch.empty(self.Z, **f64),
+                           torch.empty(self.Z, **f64), torch.empty(self.Z, **f64), torch.empty(self.N, **i32),
+                           torch.empty(self.N, **i32))
+
+    def unpack(self, out: FlashResult, s: int):
+        """System s's results as NumPy arrays (x, y, K shaped [nc, n])."""
+        a, b = int(self.off[s]), int(self.off[s + 1])
+        za, zb = int(self.zoff[s]), int(self.zoff[s + 1])
+        nc, n = int(self.nc[s]), int(self.n[s])
+        cpu = lambda t, lo, hi: t[lo:hi].cpu().numpy()
+        return dict(nphase=cpu(out.nphase, a, b), beta=cpu(out.beta, a, b), status=cpu(out.status, a, b),
+                    iters=cpu(out.iters, a, b), x=cpu(out.x, za, zb).reshape(nc, n), y=cpu(out.y, za, zb).reshape(nc, n),
+                    K=cpu(out.K, za, zb).reshape(nc, n))
+
+    def ptflash_batch_flash(self, P, T, z, out: FlashResult | None = None, stream=None) -> FlashResult:
+        out = out or self.alloc_outputs(P.device)
+        _check(load().ptflash_batch_flash(self._h, _ptr(P), _ptr(T), _ptr(z), _ptr(out.nphase), _ptr(out.beta),
+                                          _ptr(out.x), _ptr(out.y), _ptr(out.K), _ptr(out.status), _ptr(out.iters),
+                                          _stream_handle(stream)))
+        return out
+
+    def ptflash_batch_tune(self, P, T, z, out: FlashResult | None = None):
+        """Returns ({nc: blocks per SM (0 = default)}, {nc: best group ms})."""
+        out = out or self.alloc_outputs(P.device)
+        bps = (ctypes.c_int32 * 17)()
+        ms = (ctypes.c_float * 17)()
+        _check(load().ptflash_batch_tune(self._h, _ptr(P), _ptr(T), _ptr(z), _ptr(out.nphase), _ptr(out.beta),
+                                         _ptr(out.x), _ptr(out.y), _ptr(out.K), _ptr(out.status), _ptr(out.iters),
+                                         bps, ms))
+        present = sorted(set(int(k) for k, m in zip(self.nc, self.n) if m > 0))
+        return {k: int(bps[k]) for k in present}, {k: float(ms[k]) for k in present}
+
+    def ptflash_batch_info(self):
+        g, nodes, n = ctypes.c_int32(), _I64(), _I64()
+        _check(load().ptflash_batch_info(self._h, ctypes.byref(g), ctypes.byref(nodes), ctypes.byref(n)))
+        return dict(groups=g.value, graph_nodes=nodes.value, mixtures=n.value)

@@ -9,6 +9,8 @@ Workloads (sizes named by what they are):
   * ``nc8_1e6``  -- 8 pseudo-components, 1e6 mixtures, z ~ Dirichlet(0.5)
   * ``nc10_2phase_1e6`` -- 10 pseudo-components, T in [250, 450] K,
     P in [2, 15] MPa, z ~ Dirichlet(1) (two-phase-biased conditions)
+  * ``uneven_systems()`` -- 64 fluid systems with nc ~ U{3..16}, each its
+    own pseudo-components, 62,500 mixtures each (4e6 in all)
 Pseudo-components: Tc ~ U(150, 650) K sorted ascending, Pc ~ U(2, 5) MPa,
 omega ~ U(0, 0.5), symmetric k_ij ~ U(0, 0.1) with zero diagonal.  The paper's
 own case-study data are synthetic too (Sec. 2.4: LHS + Dirichlet draws);
@@ -95,6 +97,23 @@ def workload(name: str, n: int | None = None):
     cond = conditions(w["nc"], n if n is not None else w["n"], w["cond_seed"], w["T_range"], w["P_range"],
                       w["alpha"])
     return comp, cond
+
+
+def uneven_systems(n_sys: int = 64, n_per: int = 62_500, seed: int = 2, nc_range=(3, 16), n_list=None):
+    """Uneven batch: n_sys fluid systems with nc ~ U{nc_range} each, every
+    system its own pseudo-components (drawn as above, seed [seed, s, 0]) and
+    conditions T ~ U(200, 600) K, P ~ U(0.1, 20) MPa, z ~ Dirichlet(1) (seed
+    [seed, s, 1]); n_per mixtures per system unless n_list gives them.
+    Returns a list of (Components, Conditions)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    ncs = g.integers(nc_range[0], nc_range[1] + 1, n_sys)
+    out = []
+    for s in range(n_sys):
+        n = int(n_list[s]) if n_list is not None else n_per
+        comp = pseudo_components(int(ncs[s]), [seed, s, 0])
+        cond = conditions(int(ncs[s]), n, [seed, s, 1])
+        out.append((comp, cond))
+    return out
 
 
 # Paper Table 1 (Sec. 2.3): Pc [MPa], Tc [K], omega of the nine components;
