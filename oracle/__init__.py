@@ -75,6 +75,11 @@ def _lib_handle():
         lib.oracle_rr.restype = ctypes.c_int
         lib.oracle_tr_subproblem.argtypes = [ctypes.c_int, _D, _D, _D, ctypes.c_double, _D]
         lib.oracle_tr_subproblem.restype = ctypes.c_double
+        lib.oracle_dlnphi_dPT.argtypes = sysargs + [ctypes.c_double, ctypes.c_double, _D, _D, _D]
+        lib.oracle_dlnphi_dPT.restype = ctypes.c_int
+        lib.oracle_flash_jacobian_batch.argtypes = sysargs + [ctypes.c_int64, _D, _D, _D, _I, _D, _D, _D, _D, _I,
+                                                              ctypes.c_int]
+        lib.oracle_flash_jacobian_batch.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -213,3 +218,30 @@ def tr_subproblem(H, g, radius, mdiag=None):
     md = _f64(mdiag) if mdiag is not None else None
     pred = _lib_handle().oracle_tr_subproblem(len(g), _p(H), _p(g), _p(md), radius, _p(d))
     return d, pred
+
+
+def dlnphi_dPT(sysc: System, P: float, T: float, c):
+    """d ln phi_i / dP and d ln phi_i / dT at fixed composition c."""
+    c = _f64(c)
+    dP = np.zeros(sysc.nc)
+    dT = np.zeros(sysc.nc)
+    _lib_handle().oracle_dlnphi_dPT(*sysc._args(), P, T, _p(c), _p(dP), _p(dT))
+    return dP, dT
+
+
+def flash_jacobian(sysc: System, P, T, z, res, nthreads: int | None = None):
+    """Jacobian of (beta, x, y) with respect to (P, T, z) at the converged
+    results `res` (a flash() dict): array [n, 1 + 2 nc, nc + 2] (rows beta,
+    x_1..x_nc, y_1..y_nc; columns P, T, z_1..z_nc, z read as mole numbers) and
+    ok[n] (0, or -1 where the split Hessian is singular)."""
+    P, T, z = _f64(P), _f64(T), _f64(z)
+    n, nc = P.shape[0], sysc.nc
+    jac = np.zeros((n, 1 + 2 * nc, nc + 2))
+    ok = np.zeros(n, np.int32)
+    nph = np.ascontiguousarray(res["nphase"], np.int32)
+    rc = _lib_handle().oracle_flash_jacobian_batch(*sysc._args(), n, _p(P), _p(T), _p(z), _pi(nph),
+                                                   _p(_f64(res["beta"])), _p(_f64(res["x"])), _p(_f64(res["y"])),
+                                                   _p(jac), _pi(ok), nthreads or default_threads())
+    if rc:
+        raise ValueError("oracle_flash_jacobian_batch failed")
+    return jac, ok

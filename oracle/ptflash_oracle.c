@@ -1101,3 +1101,200 @@ int oracle_stability_batch(int nc, const double* Tc, const double* Pc, const dou
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sensitivities of the converged flash (the implicit-function-theorem idea  */
+/* the paper applies to Rachford-Rice in Sec. 4.2.2, applied to the whole   */
+/* equilibrium).  Parity unpinned by the paper itself (it prints no          */
+/* derivative values); pinned in the tests by central finite differences of  */
+/* this oracle's flash and by the binary phase rule.                         */
+/* ------------------------------------------------------------------------ */
+
+/* d ln phi_i / dP and d ln phi_i / dT at fixed composition c (Appendix A,
+ * Eqs. a_i, b_i, alpha_i, lnphi differentiated by hand).  With
+ * s = P: d ln A_i = 1/P, d ln B_i = 1/P;
+ * s = T: d ln A_i = 2 a'/a - 2/T (a = 1 + m (1 - sqrt(T/Tc)),
+ *        a' = -m / (2 sqrt(T Tc))), d ln B_i = -1/T.
+ * A_ij = (1 - k_ij) sqrt(A_i A_j) gives dA_ij = A_ij (d ln A_i + d ln A_j)/2;
+ * psi_i = sum_j A_ij c_j, A = sum c_i psi_i, B = sum c_i B_i; the root moves
+ * with dZ = -(F_A dA + F_B dB) / F_Z on F = Z^3 - Z^2 + (A - B - B^2) Z - AB;
+ * ln phi_i = bb_i (Z - 1) - ln(Z - B) + q_i L, bb_i = B_i/B,
+ * q_i = (A bb_i - 2 psi_i)/B, L = ln(1 + B/Z). */
+void or_dlnphi_dPT(const or_sys* s, double P, double T, const double* c, double* dP, double* dT) {
+    int nc = s->nc;
+    or_mix m;
+    or_mix_init(s, P, T, &m);
+    or_phase ph;
+    or_eos(&m, c, &ph);
+    double A = ph.A, B = ph.B, Z = ph.Z;
+    double L = log(1.0 + B / Z);
+    double FZ = 3.0 * Z * Z - 2.0 * Z + A - B - B * B, FA = Z - B, FB = -Z - 2.0 * B * Z - A;
+    for (int which = 0; which < 2; which++) {
+        double lA[OR_MAXNC], lB[OR_MAXNC];
+        for (int i = 0; i < nc; i++) {
+            if (which == 0) {
+                lA[i] = 1.0 / P;
+                lB[i] = 1.0 / P;
+            } else {
+                double mi = 0.480 + 1.574 * s->om[i] - 0.176 * s->om[i] * s->om[i];
+                double a = 1.0 + mi * (1.0 - sqrt(T / s->Tc[i]));
+                double ap = -mi / (2.0 * sqrt(T * s->Tc[i]));
+                lA[i] = 2.0 * ap / a - 2.0 / T;
+                lB[i] = -1.0 / T;
+            }
+        }
+        double dpsi[OR_MAXNC], dA = 0.0, dB = 0.0;
+        for (int i = 0; i < nc; i++) {
+            double t = 0.0;
+            for (int j = 0; j < nc; j++) t += m.Aij[i * nc + j] * 0.5 * (lA[i] + lA[j]) * c[j];
+            dpsi[i] = t;
+        }
+        for (int i = 0; i < nc; i++) {
+            dA += c[i] * dpsi[i];
+            dB += c[i] * m.Bi[i] * lB[i];
+        }
+        double dZ = -(FA * dA + FB * dB) / FZ;
+        double dL = (dB * Z - B * dZ) / (Z * (Z + B));
+        double* out = which == 0 ? dP : dT;
+        for (int i = 0; i < nc; i++) {
+            double bb = m.Bi[i] / B;
+            double dbb = (m.Bi[i] * lB[i] * B - m.Bi[i] * dB) / (B * B);
+            double q = (A * bb - 2.0 * ph.psi[i]) / B;
+            double dq = ((dA * bb + A * dbb - 2.0 * dpsi[i]) * B - (A * bb - 2.0 * ph.psi[i]) * dB) / (B * B);
+            out[i] = dbb * (Z - 1.0) + bb * dZ - (dZ - dB) / (Z - B) + dq * L + q * dL;
+        }
+    }
+}
+
+/* Solve M u = r (n x n, row-major) by Gaussian elimination with partial
+ * pivoting; returns -1 if a pivot vanishes. */
+static int gauss_solve(int n, const double* Min, const double* r, double* u) {
+    double M[OR_MAXNC * OR_MAXNC], b[OR_MAXNC];
+    memcpy(M, Min, sizeof(double) * n * n);
+    memcpy(b, r, sizeof(double) * n);
+    for (int k = 0; k < n; k++) {
+        int p = k;
+        for (int i = k + 1; i < n; i++)
+            if (fabs(M[i * n + k]) > fabs(M[p * n + k])) p = i;
+        if (!(fabs(M[p * n + k]) > 0.0)) return -1;
+        if (p != k) {
+            for (int j = 0; j < n; j++) { double t = M[k * n + j]; M[k * n + j] = M[p * n + j]; M[p * n + j] = t; }
+            double t = b[k]; b[k] = b[p]; b[p] = t;
+        }
+        for (int i = k + 1; i < n; i++) {
+            double f = M[i * n + k] / M[k * n + k];
+            for (int j = k; j < n; j++) M[i * n + j] -= f * M[k * n + j];
+            b[i] -= f * b[k];
+        }
+    }
+    for (int i = n - 1; i >= 0; i--) {
+        double t = b[i];
+        for (int j = i + 1; j < n; j++) t -= M[i * n + j] * u[j];
+        u[i] = t / M[i * n + i];
+    }
+    return 0;
+}
+
+/* Forward Jacobian of the flash result (beta, x, y) with respect to
+ * (P, T, z) at a converged result, the feed z read as mole numbers (the
+ * result depends on z / sum z only).  Unknowns v = vapour moles, l = z - v;
+ * V = sum v = beta S, L = sum l = (1 - beta) S, S = sum z.  Equilibrium
+ * g_i = ln y_i + ln phi_i^V(y) - ln x_i - ln phi_i^L(x) = 0 (Eq. eq_cond),
+ * so dv = -H^{-1} (dg/dtheta) dtheta with
+ *   H = A^V + A^L, A^V = (diag(1/y) - 1 + J^V)/V, A^L = (diag(1/x) - 1 + J^L)/L
+ *   (J = n_T d ln phi / dn, the Hessian of G in n^V, reading R5),
+ *   dg/dz = -A^L, dg/dP = d ln phi^V/dP - d ln phi^L/dP (same for T);
+ * then d beta = (sum dv - beta sum dz)/S, dy = (dv - y sum dv)/V,
+ * dx = (dz - dv - x (sum dz - sum dv))/L.
+ * Single phase: beta = 0 and x = y = z/S, so dx_i/dz_j = dy_i/dz_j =
+ * (delta_ij - z_i/S)/S and the P, T columns vanish.
+ * jac: row-major [(1 + 2 nc) x (nc + 2)], rows beta, x_1..x_nc, y_1..y_nc;
+ * columns P, T, z_1..z_nc.  Returns 0, or -1 if H is singular. */
+int or_flash_jacobian(const or_sys* s, double P, double T, const double* z, int nphase, double beta, const double* x,
+                      const double* y, double* jac) {
+    int nc = s->nc, nr = 1 + 2 * nc, ncol = nc + 2;
+    double S = 0.0;
+    for (int i = 0; i < nc; i++) S += z[i];
+    for (int k = 0; k < nr * ncol; k++) jac[k] = 0.0;
+    if (nphase != 2) {
+        for (int i = 0; i < nc; i++)
+            for (int j = 0; j < nc; j++) {
+                double d = ((i == j ? 1.0 : 0.0) - z[i] / S) / S;
+                jac[(1 + i) * ncol + 2 + j] = d;
+                jac[(1 + nc + i) * ncol + 2 + j] = d;
+            }
+        return 0;
+    }
+    double V = beta * S, Lm = (1.0 - beta) * S;
+    or_mix m;
+    or_mix_init(s, P, T, &m);
+    or_phase pl, pv;
+    or_eos(&m, x, &pl);
+    or_eos(&m, y, &pv);
+    double JL[OR_MAXNC * OR_MAXNC], JV[OR_MAXNC * OR_MAXNC], AL[OR_MAXNC * OR_MAXNC], H[OR_MAXNC * OR_MAXNC];
+    or_dlnphi_dn(&m, x, &pl, JL);
+    or_dlnphi_dn(&m, y, &pv, JV);
+    for (int i = 0; i < nc; i++)
+        for (int j = 0; j < nc; j++) {
+            double av = ((i == j ? 1.0 / y[i] : 0.0) - 1.0 + JV[i * nc + j]) / V;
+            AL[i * nc + j] = ((i == j ? 1.0 / x[i] : 0.0) - 1.0 + JL[i * nc + j]) / Lm;
+            H[i * nc + j] = av + AL[i * nc + j];
+        }
+    double dPL[OR_MAXNC], dTL[OR_MAXNC], dPV[OR_MAXNC], dTV[OR_MAXNC];
+    or_dlnphi_dPT(s, P, T, x, dPL, dTL);
+    or_dlnphi_dPT(s, P, T, y, dPV, dTV);
+    for (int col = 0; col < ncol; col++) {
+        double rhs[OR_MAXNC], dv[OR_MAXNC], dz[OR_MAXNC];
+        for (int i = 0; i < nc; i++) {
+            dz[i] = (col >= 2 && i == col - 2) ? 1.0 : 0.0;
+            if (col == 0) rhs[i] = dPV[i] - dPL[i];
+            else if (col == 1) rhs[i] = dTV[i] - dTL[i];
+            else rhs[i] = -AL[i * nc + (col - 2)];
+        }
+        if (gauss_solve(nc, H, rhs, dv)) return -1;
+        double sdv = 0.0, sdz = 0.0;
+        for (int i = 0; i < nc; i++) {
+            dv[i] = -dv[i];
+            sdv += dv[i];
+            sdz += dz[i];
+        }
+        jac[col] = (sdv - beta * sdz) / S;
+        for (int i = 0; i < nc; i++) {
+            jac[(1 + i) * ncol + col] = (dz[i] - dv[i] - x[i] * (sdz - sdv)) / Lm;
+            jac[(1 + nc + i) * ncol + col] = (dv[i] - y[i] * sdv) / V;
+        }
+    }
+    return 0;
+}
+
+int oracle_dlnphi_dPT(int nc, const double* Tc, const double* Pc, const double* om, const double* kij, double P,
+                      double T, const double* c, double* dP, double* dT) {
+    if (nc < 2 || nc > OR_MAXNC) return -1;
+    or_sys s;
+    sys_from(nc, Tc, Pc, om, kij, &s);
+    or_dlnphi_dPT(&s, P, T, c, dP, dT);
+    return 0;
+}
+
+/* Batch of Jacobians at given converged results (component-major arrays
+ * [i * n + k]); jac: [n][(1 + 2 nc)(nc + 2)]; ok[k] = 0 or -1 (singular H). */
+int oracle_flash_jacobian_batch(int nc, const double* Tc, const double* Pc, const double* om, const double* kij,
+                                int64_t n, const double* P, const double* T, const double* z, const int32_t* nphase,
+                                const double* beta, const double* x, const double* y, double* jac, int32_t* ok,
+                                int nthreads) {
+    if (nc < 2 || nc > OR_MAXNC) return -1;
+    or_sys s;
+    sys_from(nc, Tc, Pc, om, kij, &s);
+    int64_t sz = (int64_t)(1 + 2 * nc) * (nc + 2);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+    for (int64_t k = 0; k < n; k++) {
+        double zz[OR_MAXNC], xx[OR_MAXNC], yy[OR_MAXNC];
+        for (int i = 0; i < nc; i++) {
+            zz[i] = z[(int64_t)i * n + k];
+            xx[i] = x[(int64_t)i * n + k];
+            yy[i] = y[(int64_t)i * n + k];
+        }
+        ok[k] = or_flash_jacobian(&s, P[k], T[k], zz, nphase[k], beta[k], xx, yy, jac + k * sz);
+    }
+    return 0;
+}
