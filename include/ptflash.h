@@ -172,6 +172,29 @@ int ptflash_flash_noalloc(int nc, const double* Tc, const double* Pc, const doub
                           void* stream);
 
 /*
+ * Reverse-mode sensitivities of the flash result (beta, x, y) with respect to
+ * (P, T, z): the implicit-function-theorem step the paper applies to the
+ * Rachford-Rice root (Sec. 4.2.2) applied to the equilibrium of Eq. eq_cond
+ * at the converged split.  The feed is read as mole numbers (the flash
+ * depends on z / sum z).  For the functional l = gbeta.beta + gx.x + gy.y
+ * summed per mixture, writes dl/dP to gP[n], dl/dT to gT[n] and dl/dz to
+ * gz[nc * n] (component-major).  Two-phase mixtures: one solve with the Hessian
+ * of G in n^V (Eq. split_hess) at the given x, y; single-phase mixtures
+ * (x = y = z / sum z, beta = 0): gz_j = (g_j - sum_i g_i z_i / S) / S with
+ * g = gx + gy, S = sum z, and gP = gT = 0.
+ * Inputs: DEVICE P, T, z and the results nphase, beta, x, y of ptflash_flash
+ * on them (converged results; the sensitivities of a MAXITER result are
+ * those of the point it stopped at).  gbeta[n], gx[nc * n], gy[nc * n] may
+ * each be NULL (zero).  astatus[n] (optional): 0 two-phase, 1 single phase,
+ * 2 split Hessian not positive definite (that mixture's outputs are NaN).
+ * Same context, stream and ownership rules as ptflash_flash.
+ */
+int ptflash_flash_adjoint(ptflash_ctx* c, int64_t n, const double* P, const double* T, const double* z,
+                          const int32_t* nphase, const double* beta, const double* x, const double* y,
+                          const double* gbeta, const double* gx, const double* gy, double* gP, double* gT,
+                          double* gz, int32_t* astatus, void* stream);
+
+/*
  * Uneven batches: many fluid systems, each with its own number of components
  * (2..16), component data and mixtures, flashed by one CUDA graph launch.  The
  * paper flashes batches of one fluid system (Sec. 3); a batch of systems is

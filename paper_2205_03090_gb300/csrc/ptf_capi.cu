@@ -230,6 +230,28 @@ int ptflash_flash(ptflash_ctx* c, int64_t n, const double* P, const double* T, c
     return run(c, n, P, T, z, nphase, beta, x, y, K, status, iters, mode, true, (cudaStream_t)stream, p_l, p_r);
 }
 
+int ptflash_flash_adjoint(ptflash_ctx* c, int64_t n, const double* P, const double* T, const double* z,
+                          const int32_t* nphase, const double* beta, const double* x, const double* y,
+                          const double* gbeta, const double* gx, const double* gy, double* gP, double* gT,
+                          double* gz, int32_t* astatus, void* stream) {
+    if (!c) return PTF_ERR_INVALID_ARG;
+    if (!c->have_comp) return PTF_ERR_NOT_READY;
+    if (n < 0) return PTF_ERR_INVALID_ARG;
+    if (n == 0) return PTF_OK;
+    if (!P || !T || !z || !nphase || !beta || !x || !y || !gP || !gT || !gz) return PTF_ERR_INVALID_ARG;
+    AdjIO a{n, P, T, z, nphase, beta, x, y, gbeta, gx, gy, gP, gT, gz, astatus};
+    const int grid = c->sm_count * 8;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (c->comp.nc) {
+#define PTF_CASE(NC) \
+    case NC: PTF_CUDA(launch_adjoint<NC>(c->comp, a, grid, s)); return PTF_OK;
+        PTF_CASE(2) PTF_CASE(3) PTF_CASE(4) PTF_CASE(5) PTF_CASE(6) PTF_CASE(7) PTF_CASE(8) PTF_CASE(9)
+        PTF_CASE(10) PTF_CASE(11) PTF_CASE(12) PTF_CASE(13) PTF_CASE(14) PTF_CASE(15) PTF_CASE(16)
+#undef PTF_CASE
+    }
+    return PTF_ERR_UNSUPPORTED;
+}
+
 int ptflash_stability(ptflash_ctx* c, int64_t n, const double* P, const double* T, const double* z,
                       int32_t* stable, double* tm_min, double* K, int32_t* status, void* stream) {
     if (!c) return PTF_ERR_INVALID_ARG;

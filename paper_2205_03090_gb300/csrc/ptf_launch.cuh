@@ -4,6 +4,7 @@
 #include "ptf_kernels.cuh"
 #include "ptf_comp.cuh"
 #include "ptf_mlp.cuh"
+#include "ptf_adjoint.cuh"
 
 namespace ptf {
 
@@ -99,7 +100,8 @@ cudaError_t launch_many(const Comp<NC>* tab, const int32_t* sys, const WS& ws, c
     extern template cudaError_t launch_plain<NC>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, \
                                                  cudaEvent_t*, const MLP*, float, float);                        \
     extern template cudaError_t launch_many<NC>(const Comp<NC>*, const int32_t*, const WS&, const IO&, int, int, \
-                                                int, cudaStream_t);
+                                                int, cudaStream_t);                                              \
+    extern template cudaError_t launch_adjoint<NC>(const CompHost&, const AdjIO&, int, cudaStream_t);
 PTF_DECLARE_NC(2) PTF_DECLARE_NC(3) PTF_DECLARE_NC(4) PTF_DECLARE_NC(5) PTF_DECLARE_NC(6) PTF_DECLARE_NC(7)
 PTF_DECLARE_NC(8) PTF_DECLARE_NC(9) PTF_DECLARE_NC(10) PTF_DECLARE_NC(11) PTF_DECLARE_NC(12) PTF_DECLARE_NC(13)
 PTF_DECLARE_NC(14) PTF_DECLARE_NC(15) PTF_DECLARE_NC(16)
@@ -110,6 +112,7 @@ PTF_DECLARE_NC(14) PTF_DECLARE_NC(15) PTF_DECLARE_NC(16)
     template cudaError_t launch_plain<NC>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*, \
                                           const MLP*, float, float);                                               \
     template cudaError_t launch_many<NC>(const Comp<NC>*, const int32_t*, const WS&, const IO&, int, int, int,     \
-                                         cudaStream_t);
+                                         cudaStream_t);                                                            \
+    template cudaError_t launch_adjoint<NC>(const CompHost&, const AdjIO&, int, cudaStream_t);
 
 }  // namespace ptf

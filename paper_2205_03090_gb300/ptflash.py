@@ -74,6 +74,8 @@ def load(path: str = LIB_PATH):
     for f in ("ptflash_nn_set", "ptflash_nn_get", "ptflash_nn_features", "ptflash_nn_infer", "ptflash_nn_train_steps",
               "ptflash_nn_eval"):
         getattr(lib, f).restype = ctypes.c_int
+    lib.ptflash_flash_adjoint.argtypes = [_VP, _I64] + [_VP] * 15
+    lib.ptflash_flash_adjoint.restype = ctypes.c_int
     _I32P = ctypes.POINTER(ctypes.c_int32)
     lib.ptflash_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, _I32P, ctypes.POINTER(_I64), _D, _D, _D,
                                          _D]
@@ -206,6 +208,23 @@ class Flash:
         _check(load().ptflash_stability(self._h, n, _ptr(P), _ptr(T), _ptr(z), _ptr(stable), _ptr(tm), _ptr(K),
                                         _ptr(status), _stream_handle(stream)))
         return stable, tm, K, status
+
+    def ptflash_flash_adjoint(self, P, T, z, res: FlashResult, gbeta=None, gx=None, gy=None, stream=None):
+        """dl/dP, dl/dT, dl/dz for l = gbeta.beta + gx.x + gy.y at the flash
+        results `res` of (P, T, z); returns (gP[n], gT[n], gz[nc, n], astatus[n])."""
+        import torch
+        n = int(P.shape[0])
+        dev = P.device
+        gP = torch.empty(n, dtype=torch.float64, device=dev)
+        gT = torch.empty(n, dtype=torch.float64, device=dev)
+        gz = torch.empty(self.nc, n, dtype=torch.float64, device=dev)
+        ast = torch.empty(n, dtype=torch.int32, device=dev)
+        c = lambda t: t.contiguous() if t is not None else None
+        gbeta, gx, gy = c(gbeta), c(gx), c(gy)
+        _check(load().ptflash_flash_adjoint(self._h, n, _ptr(P), _ptr(T), _ptr(z), _ptr(res.nphase), _ptr(res.beta),
+                                            _ptr(res.x), _ptr(res.y), _ptr(gbeta), _ptr(gx), _ptr(gy), _ptr(gP),
+                                            _ptr(gT), _ptr(gz), _ptr(ast), _stream_handle(stream)))
+        return gP, gT, gz, ast
 
     STAGES = ("prep_precheck", "stab_ss", "stab_tr", "stab_decide", "split_ss", "split_tr")
 

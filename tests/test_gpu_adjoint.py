@@ -1,0 +1,198 @@
+"""Implicit-function-theorem adjoint (ptflash_flash_adjoint) against the
+oracle's forward Jacobian and central finite differences of the GPU flash
+itself, on the 10-component two-phase-biased workload (T 250-450 K, P 2-15
+MPa, z ~ Dirichlet(1))."""
+import numpy as np
+import pytest
+
+from paper_2205_03090_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ptf():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2205_03090_gb300 import build, ptflash
+    build.build()
+    ptflash.load()
+    return ptflash
+
+
+def _setup(ptf, n, name="nc10_2phase_1e6"):
+    import torch
+    comp, cond = wl.workload(name, n)
+    fl = ptf.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=max(n, 1 << 16))
+    P, T, z = (torch.tensor(a, device="cuda") for a in (cond.P, cond.T, cond.z))
+    z = z.contiguous()
+    res = fl.ptflash_flash(P, T, z)
+    torch.cuda.synchronize()
+    return comp, cond, fl, P, T, z, res
+
+
+def _gpu_jacobian_rows(fl, P, T, z, res, nc):
+    """Row r of d(beta, x, y)/d(P, T, z) for every mixture, from the adjoint
+    with unit upstream vectors: [n, 1 + 2 nc, nc + 2]."""
+    import torch
+    n = int(P.shape[0])
+    J = np.zeros((n, 1 + 2 * nc, nc + 2))
+    ast = None
+    for r in range(1 + 2 * nc):
+        gb = torch.zeros(n, dtype=torch.float64, device="cuda")
+        gx = torch.zeros(nc, n, dtype=torch.float64, device="cuda")
+        gy = torch.zeros(nc, n, dtype=torch.float64, device="cuda")
+        if r == 0:
+            gb[:] = 1.0
+        elif r <= nc:
+            gx[r - 1] = 1.0
+        else:
+            gy[r - 1 - nc] = 1.0
+        gP, gT, gz, ast = fl.ptflash_flash_adjoint(P, T, z, res, gb, gx, gy)
+        torch.cuda.synchronize()
+        J[:, r, 0] = gP.cpu().numpy()
+        J[:, r, 1] = gT.cpu().numpy()
+        J[:, r, 2:] = gz.cpu().numpy().T
+    return J, ast.cpu().numpy()
+
+
+def _oracle_jac_at(oracle_mod, comp, cond, res):
+    s = oracle_mod.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
+    g = {k: getattr(res, k).cpu().numpy() for k in ("nphase", "beta", "x", "y")}
+    return oracle_mod.flash_jacobian(s, cond.P, cond.T, cond.z, g)
+
+
+def test_adjoint_rows_match_oracle_jacobian(ptf, oracle_mod):
+    comp, cond, fl, P, T, z, res = _setup(ptf, 3000)
+    nc = comp.nc
+    J, ast = _gpu_jacobian_rows(fl, P, T, z, res, nc)
+    Jo, ok = _oracle_jac_at(oracle_mod, comp, cond, res)
+    nph = res.nphase.cpu().numpy()
+    assert set(np.unique(ast)) <= {0, 1, 2}
+    assert ((ast == 1) == (nph != 2)).all()
+    sel = (ok == 0) & (ast != 2)
+    assert sel.mean() > 0.99
+    # column-wise relative error (P, T, z columns carry different units)
+    scale = np.maximum(np.abs(Jo).max(axis=1, keepdims=True), 1e-300)
+    err = (np.abs(J - Jo) / scale).max(axis=(1, 2))[sel]
+    print("adjoint vs oracle Jacobian: max", err.max(), "99.9%", np.quantile(err, 0.999), "two-phase",
+          int((nph == 2).sum()))
+    assert np.quantile(err, 0.999) < 1e-8 and err.max() < 1e-6
+
+
+def test_adjoint_vector_jacobian_products(ptf, oracle_mod):
+    import torch
+    comp, cond, fl, P, T, z, res = _setup(ptf, 2000)
+    nc, n = comp.nc, cond.n
+    rng = np.random.default_rng(9)
+    wb, wx, wy = rng.normal(size=n), rng.normal(size=(nc, n)), rng.normal(size=(nc, n))
+    gP, gT, gz, ast = fl.ptflash_flash_adjoint(P, T, z, res, *(torch.tensor(a, device="cuda") for a in (wb, wx, wy)))
+    torch.cuda.synchronize()
+    Jo, ok = _oracle_jac_at(oracle_mod, comp, cond, res)
+    w = np.concatenate([wb[None], wx, wy], axis=0).T  # [n, 1 + 2 nc]
+    vjp = np.einsum("nr,nrc->nc", w, Jo)
+    got = np.concatenate([gP.cpu().numpy()[:, None], gT.cpu().numpy()[:, None], gz.cpu().numpy().T], axis=1)
+    sel = (ok == 0) & (ast.cpu().numpy() != 2)
+    scale = np.maximum(np.einsum("nr,nrc->nc", np.abs(w), np.abs(Jo)), 1e-300)
+    err = (np.abs(got - vjp) / scale).max(axis=1)[sel]
+    print("vjp: max rel", err.max())
+    assert np.quantile(err, 0.999) < 1e-8 and err.max() < 1e-6
+
+
+def test_adjoint_matches_gpu_finite_differences(ptf):
+    """Central differences (relative step 1e-6) of the GPU flash itself, all
+    perturbed copies in one batch; the feed perturbation is renormalised."""
+    import torch
+    comp, cond, fl, P, T, z, res = _setup(ptf, 4000)
+    nc = comp.nc
+    nph = res.nphase.cpu().numpy()
+    st = res.status.cpu().numpy()
+    K = res.K.cpu().numpy()
+    idx = np.nonzero((nph == 2) & ((st & 16) == 0) & (np.abs(np.log(K)).max(axis=0) > 0.3))[0][:150]
+    m = len(idx)
+    ncol = nc + 2
+    Pn, Tn, zn = cond.P[idx], cond.T[idx], cond.z[:, idx]
+    Pb = np.repeat(Pn[None], 2 * ncol, 0)
+    Tb = np.repeat(Tn[None], 2 * ncol, 0)
+    zb = np.repeat(zn[None], 2 * ncol, 0)  # [2 ncol, nc, m]
+    hs = np.zeros((ncol, m))
+    for c in range(ncol):
+        for sgn, row in ((1, 2 * c), (-1, 2 * c + 1)):
+            if c == 0:
+                h = 1e-6 * Pn
+                Pb[row] = Pn + sgn * h
+            elif c == 1:
+                h = 1e-6 * Tn
+                Tb[row] = Tn + sgn * h
+            else:
+                h = 1e-6 * zn[c - 2]
+                zz = zn.copy()
+                zz[c - 2] += sgn * h
+                zb[row] = zz / zz.sum(axis=0, keepdims=True)
+            hs[c] = h
+    flat = lambda a: np.ascontiguousarray(a.reshape(a.shape[0] * a.shape[-1]) if a.ndim == 2 else a)
+    Pf, Tf = flat(Pb), flat(Tb)
+    zf = np.ascontiguousarray(zb.transpose(1, 0, 2).reshape(nc, -1))
+    d = [torch.tensor(a, device="cuda") for a in (Pf, Tf, zf)]
+    r = fl.ptflash_flash(d[0], d[1], d[2].contiguous())
+    torch.cuda.synchronize()
+    v = np.concatenate([r.beta.cpu().numpy()[None], r.x.cpu().numpy(), r.y.cpu().numpy()], 0)  # [1+2nc, 2 ncol m]
+    v = v.reshape(1 + 2 * nc, 2 * ncol, m)
+    both2 = (r.nphase.cpu().numpy().reshape(2 * ncol, m) == 2).all(axis=0)
+    fd = np.zeros((m, 1 + 2 * nc, ncol))
+    for c in range(ncol):
+        fd[:, :, c] = ((v[:, 2 * c] - v[:, 2 * c + 1]) / (2 * hs[c])).T
+    Pg, Tg, zg = (t[idx].contiguous() if t.dim() == 1 else t[:, idx].contiguous() for t in (P, T, z))
+    sub = ptf.FlashResult(*(None if t is None else (t[idx].contiguous() if t.dim() == 1 else t[:, idx].contiguous())
+                            for t in (res.nphase, res.beta, res.x, res.y, res.K, res.status, res.iters)))
+    J, ast = _gpu_jacobian_rows(fl, Pg, Tg, zg, sub, nc)
+    scale = np.maximum(np.abs(J).max(axis=1, keepdims=True), 1e-12)
+    err = (np.abs(fd - J) / scale).max(axis=(1, 2))[both2]
+    print("GPU FD vs adjoint: median", np.median(err), "max", err.max(), "of", len(err))
+    assert len(err) > 100 and np.median(err) < 1e-6 and err.max() < 1e-4
+
+
+def test_autograd_function(ptf):
+    import torch
+    from paper_2205_03090_gb300 import autograd as ag
+    comp, cond, fl, P, T, z, res = _setup(ptf, 1000)
+    P = P.clone().requires_grad_(True)
+    T = T.clone().requires_grad_(True)
+    z = z.clone().requires_grad_(True)
+    beta, x, y, nph = ag.flash(P, T, z, fl)
+    rng = np.random.default_rng(4)
+    wb = torch.tensor(rng.normal(size=beta.shape), device="cuda")
+    wx = torch.tensor(rng.normal(size=x.shape), device="cuda")
+    loss = (wb * beta).sum() + (wx * x).sum() + y[0].sum()
+    gP, gT, gz = torch.autograd.grad(loss, (P, T, z))
+    wy = torch.zeros_like(y)
+    wy[0] = 1.0
+    eP, eT, ez, _ = fl.ptflash_flash_adjoint(P.detach(), T.detach(), z.detach(), res, wb, wx, wy)
+    assert torch.allclose(gP, eP, rtol=1e-12, atol=0, equal_nan=True)
+    assert torch.allclose(gT, eT, rtol=1e-12, atol=0, equal_nan=True)
+    assert torch.allclose(gz, ez, rtol=1e-12, atol=0, equal_nan=True)
+
+
+def test_adjoint_full_size_sampled(ptf, oracle_mod):
+    """1e6 mixtures (forward + one adjoint launch); 1000 sampled against the
+    oracle's vector-Jacobian products."""
+    import torch
+    comp, cond, fl, P, T, z, res = _setup(ptf, 1_000_000)
+    nc, n = comp.nc, cond.n
+    rng = np.random.default_rng(11)
+    wb, wx, wy = rng.normal(size=n), rng.normal(size=(nc, n)), rng.normal(size=(nc, n))
+    gP, gT, gz, ast = fl.ptflash_flash_adjoint(P, T, z, res, *(torch.tensor(a, device="cuda") for a in (wb, wx, wy)))
+    torch.cuda.synchronize()
+    idx = np.sort(rng.choice(n, 1000, replace=False))
+    s = oracle_mod.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
+    g = {k: getattr(res, k).cpu().numpy()[..., idx] for k in ("nphase", "beta", "x", "y")}
+    Jo, ok = oracle_mod.flash_jacobian(s, cond.P[idx], cond.T[idx], np.ascontiguousarray(cond.z[:, idx]), g)
+    w = np.concatenate([wb[None], wx, wy], axis=0)[:, idx].T
+    vjp = np.einsum("nr,nrc->nc", w, Jo)
+    got = np.concatenate([gP.cpu().numpy()[idx, None], gT.cpu().numpy()[idx, None], gz.cpu().numpy()[:, idx].T], 1)
+    a = ast.cpu().numpy()[idx]
+    sel = (ok == 0) & (a != 2)
+    scale = np.maximum(np.einsum("nr,nrc->nc", np.abs(w), np.abs(Jo)), 1e-300)
+    err = (np.abs(got - vjp) / scale).max(axis=1)[sel]
+    print("full size: astatus counts", np.bincount(ast.cpu().numpy(), minlength=3), "max rel", err.max())
+    assert sel.mean() > 0.99 and np.quantile(err, 0.999) < 1e-8 and err.max() < 1e-6
