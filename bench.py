@@ -152,6 +152,68 @@ def uneven_leg(args, rank, dev, flush, stream):
             "tune_seconds": round(tune_s, 2)}
 
 
+ADJOINT_DESC = ("differentiation: 10 SRK pseudo-components drawn as above, 1e6 mixtures, T~U(250,450) K, "
+                "P~U(2,15) MPa, z~Dirichlet(1); FP64 flash + implicit-function-theorem adjoint of (beta, x, y) "
+                "w.r.t. (P, T, z) for a random output functional")
+
+
+def adjoint_leg(args, rank, dev, flush, stream):
+    """Forward flash plus one adjoint launch on the 10-component workload;
+    the vector-Jacobian products checked against the oracle's forward
+    Jacobian on a sample."""
+    import torch
+    from paper_2205_03090_gb300 import ptflash, workloads as wl
+    w = wl.WORKLOADS["nc10_2phase_1e6"]
+    comp = wl.pseudo_components(w["nc"], w["comp_seed"])
+    n = w["n"]
+    cond = wl.conditions(w["nc"], n, w["cond_seed"] + 1000 * rank, w["T_range"], w["P_range"], w["alpha"])
+    fl = ptflash.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=n)
+    P = torch.tensor(cond.P, device=dev)
+    T = torch.tensor(cond.T, device=dev)
+    z = torch.tensor(cond.z, device=dev).contiguous()
+    rng = np.random.default_rng(23)
+    wb, wx, wy = (torch.tensor(a, device=dev) for a in (rng.normal(size=n), rng.normal(size=(w["nc"], n)),
+                                                        rng.normal(size=(w["nc"], n))))
+    res = fl.alloc_outputs(n, dev)
+    fwd_ms, adj_ms = [], []
+    for it in range(args.warmup + max(1, args.steps)):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        fl.ptflash_flash(P, T, z, out=res, stream=stream)
+        e[1].record(stream)
+        gP, gT, gz, ast = fl.ptflash_flash_adjoint(P, T, z, res, wb, wx, wy, stream=stream)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            fwd_ms.append(e[0].elapsed_time(e[1]))
+            adj_ms.append(e[1].elapsed_time(e[2]))
+    frac, sample = float("nan"), 0
+    if rank == 0 and args.cpu_sample > 0:
+        import oracle
+        sample = 2000
+        idx = np.sort(rng.choice(n, sample, replace=False))
+        s = oracle.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
+        g = {k: getattr(res, k).cpu().numpy()[..., idx] for k in ("nphase", "beta", "x", "y")}
+        Jo, ok = oracle.flash_jacobian(s, cond.P[idx], cond.T[idx], np.ascontiguousarray(cond.z[:, idx]), g)
+        wv = np.concatenate([wb.cpu().numpy()[None], wx.cpu().numpy(), wy.cpu().numpy()], 0)[:, idx].T
+        vjp = np.einsum("nr,nrc->nc", wv, Jo)
+        got = np.concatenate([gP.cpu().numpy()[idx, None], gT.cpu().numpy()[idx, None],
+                              gz.cpu().numpy()[:, idx].T], 1)
+        scale = np.maximum(np.einsum("nr,nrc->nc", np.abs(wv), np.abs(Jo)), 1e-300)
+        err = (np.abs(got - vjp) / scale).max(axis=1)
+        frac = float(((err <= 1e-8) & (ok == 0)).mean())
+    counts = np.bincount(ast.cpu().numpy(), minlength=3)
+    fl.close()
+    f, a = float(np.mean(fwd_ms)), float(np.mean(adj_ms))
+    return {"workload": ADJOINT_DESC, "n": n, "forward_ms": f, "adjoint_ms": a,
+            "value": n / ((f + a) / 1e3), "unit": "flashes with gradient/s",
+            "adjoint_only_value": n / (a / 1e3),
+            "oracle_match": {"frac": frac, "sample": sample, "tol": "1e-8 relative to |w|.|J| per input"},
+            "astatus": {"two_phase": int(counts[0]), "single_phase": int(counts[1]), "singular": int(counts[2])}}
+
+
 def run_oracle_sample(comp, cond, idx, nthreads=None):
     import oracle
     s = oracle.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
@@ -297,6 +359,7 @@ def ours_arm(args, ws, rank, local):
 
     learned = learned_leg(args, rank, dev, flush, stream) if args.learned_n > 0 else None
     uneven = uneven_leg(args, rank, dev, flush, stream) if args.uneven else None
+    adjoint = adjoint_leg(args, rank, dev, flush, stream) if args.adjoint else None
 
     if rank != 0:
         if dist:
@@ -350,6 +413,7 @@ def ours_arm(args, ws, rank, local):
         "clocks": clk,
         "learned": learned,
         "uneven": uneven,
+        "adjoint": adjoint,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -428,6 +492,7 @@ def main():
     ap.add_argument("--learned-n", type=int, default=10_000_000,
                     help="mixtures of the learned-form leg (0 skips it)")
     ap.add_argument("--uneven", type=int, default=1, help="run the uneven-batch leg (0 skips it)")
+    ap.add_argument("--adjoint", type=int, default=1, help="run the flash + adjoint leg (0 skips it)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
