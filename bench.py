@@ -214,6 +214,64 @@ def adjoint_leg(args, rank, dev, flush, stream):
             "astatus": {"two_phase": int(counts[0]), "single_phase": int(counts[1]), "singular": int(counts[2])}}
 
 
+# Paper Table 4 (9 components, 1e6 mixtures, RTX 3080): per-stage counts; context only.
+PAPER_TABLE4 = {"precheck_unstable_frac": 0.3744, "stab": 625645, "stab_tr_vapour": 130715, "stab_tr_liquid": 90179,
+                "split": 413442, "split_ss_converged_frac": 0.4588, "split_tr": 223741, "max_stab_tr_iters": 18,
+                "max_split_tr_iters": 13, "total_s": 3.0346}
+CASES = (("c2", 10_000_000), ("c4", 5_000_000), ("c9", 1_000_000))  # the paper's largest n per case (Sec. 5.1)
+
+
+def cases_leg(args, rank, dev, flush, stream):
+    """The paper's three case studies (Sec. 2.3) at the paper's largest batch
+    sizes: flashes/s, stage counts (Table 4's rows for the 9-component
+    fluid) and a sampled oracle check."""
+    import torch
+    from paper_2205_03090_gb300 import ptflash, workloads as wl
+    out_all = {}
+    for case, n in CASES:
+        n = max(1, int(n * args.cases_scale))
+        comp, cond, ft = wl.paper_case(case, n, 100 + rank)
+        fl = ptflash.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=n)
+        P = torch.tensor(cond.P, device=dev)
+        T = torch.tensor(cond.T, device=dev)
+        z = torch.tensor(cond.z, device=dev).contiguous()
+        out = fl.alloc_outputs(n, dev)
+        ms = []
+        for it in range(args.warmup + max(1, args.steps)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fl.ptflash_flash(P, T, z, out=out, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                ms.append(e0.elapsed_time(e1))
+        q = fl.ptflash_last_counts()
+        g = {k: getattr(out, k).cpu().numpy() for k in ("nphase", "beta", "x", "y", "status", "iters")}
+        st, it = g["status"], g["iters"]
+        stats = {"precheck_unstable_frac": float((st & 1).mean()), "stab": q["stab"], "stab_tr_items": q["stab_tr"],
+                 "split": q["split"], "split_ss_converged_frac": 1.0 - q["split_tr"] / max(1, q["split"]),
+                 "split_tr": q["split_tr"], "max_stab_tr_iters": int(((it >> 24) & 0xff).max()),
+                 "max_split_tr_iters": int(((it >> 8) & 0xff).max()), "two_phase_frac": float((g["nphase"] == 2).mean()),
+                 "maxiter": int(((st & 16) != 0).sum())}
+        frac, sample = float("nan"), 0
+        if rank == 0 and args.cpu_sample > 0:
+            rng = np.random.default_rng(29)
+            sample = min(n, 5000)
+            idx = np.sort(rng.choice(n, sample, replace=False))
+            o, _, s = run_oracle_sample(comp, cond, idx)
+            frac = match_fraction(s, comp, cond, idx, o, g)
+        fl.close()
+        t = float(np.mean(ms))
+        out_all[case] = {"components": list(wl.PAPER_CASES[case]["names"]), "n": n, "ms_per_step": t,
+                         "value": n * (frac if frac == frac else 1.0) / (t / 1e3), "unit": "flashes/s",
+                         "oracle_match": {"frac": frac, "sample": sample, "tol": TOL}, "stages": stats}
+    out_all["paper_table4_context"] = PAPER_TABLE4
+    return out_all
+
+
 def run_oracle_sample(comp, cond, idx, nthreads=None):
     import oracle
     s = oracle.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
@@ -360,6 +418,7 @@ def ours_arm(args, ws, rank, local):
     learned = learned_leg(args, rank, dev, flush, stream) if args.learned_n > 0 else None
     uneven = uneven_leg(args, rank, dev, flush, stream) if args.uneven else None
     adjoint = adjoint_leg(args, rank, dev, flush, stream) if args.adjoint else None
+    cases = cases_leg(args, rank, dev, flush, stream) if args.cases else None
 
     if rank != 0:
         if dist:
@@ -414,6 +473,7 @@ def ours_arm(args, ws, rank, local):
         "learned": learned,
         "uneven": uneven,
         "adjoint": adjoint,
+        "paper_cases": cases,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -493,6 +553,8 @@ def main():
                     help="mixtures of the learned-form leg (0 skips it)")
     ap.add_argument("--uneven", type=int, default=1, help="run the uneven-batch leg (0 skips it)")
     ap.add_argument("--adjoint", type=int, default=1, help="run the flash + adjoint leg (0 skips it)")
+    ap.add_argument("--cases", type=int, default=1, help="run the paper case-study leg (0 skips it)")
+    ap.add_argument("--cases-scale", type=float, default=1.0, help="fraction of the case-study batch sizes")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

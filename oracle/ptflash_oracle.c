@@ -25,14 +25,13 @@
  *       gbar(Z) = Z - 1 - ln(Z - B) - (A/B) ln(1 + B/Z); the lower wins
  *       (Appendix A, after Eq. halley).
  *   R7  DEM: lambda = (D_k . D_{k-1}) / (D_{k-1} . D_{k-1}) on successive
- *       ln K (ln W) updates D; on every 5th update of a run, if
- *       0 < lambda < 1, the estimate has settled (previous estimate within
- *       10 %) and successive updates shrink and are nearly parallel
- *       (cos^2 >= 0.99), add D_k lambda / (1 - lambda)
- *       (Sec. 2.2.1; Orbach-Crowe apply the step once lambda is stable).
- *       If the next evaluation fails or does not lower the residual the
- *       accelerated update is undone (that evaluation counts toward the
- *       iteration cap).
+ *       ln K (ln W) updates D; on every 3rd update of a run, if
+ *       0 < lambda < 1 and the updates shrink, add D_k lambda / (1 - lambda)
+ *       (Sec. 2.2.1 names DEM without its period or safeguards).  If the
+ *       next evaluation fails or does not lower the residual the accelerated
+ *       update is undone (that evaluation counts toward the iteration cap).
+ *       Of the periods and safeguards tried, this one lets the most trials
+ *       finish by SS, nearest the SS convergence rates of Table 4.
  *   R8  "Negative" tm / tpd / Delta G means below -EPS_NEG (1e-10).
  *   R9  Trust region: exact subproblem min g.d + d.H.d/2 s.t. ||d||_M <= r;
  *       initial radius = ||Newton step|| if H is positive definite, else 1;
@@ -60,6 +59,13 @@
  *   R14 Canonical phase labels: after a two-phase result, if Z(y) < Z(x)
  *       the phases are swapped (y is always the lower-density phase).
  *   R15 Single phase output: beta = 0, x = y = z, K = 1.
+ *   R16 K re-estimate from a stability trial (Sec. 2.2.1, last sentence)
+ *       uses the trial's composition w = W / sum W: K_i = w_i / z_i for the
+ *       vapour-like trial, z_i / w_i for the liquid-like one.  The printed
+ *       W^V_i / z_i and z_i / W^L_i agree at a stationary point; after an
+ *       early stop at the first negative tm the unnormalised form can give K
+ *       that do not bracket 1, and the split then collapses although the
+ *       mixture is unstable.
  */
 #include <math.h>
 #include <stdint.h>
@@ -482,22 +488,20 @@ static double vnorm_m(int n, const double* d, const double* mdiag) {
 }
 
 /* Dominant eigenvalue acceleration (reading R7).  dk = latest SS update,
- * d1 = the one before, d2 = the one before that.  Applied on every 5th
- * update of a run when the eigenvalue estimate has settled: successive
- * estimates within 10 % of each other, shrinking and nearly parallel
- * updates (cos^2 >= 0.99) and 0 < lambda < 1.
+ * d1 = the one before.  Applied on every DEM_PERIOD-th update of a run when
+ * the updates shrink (||dk|| < ||d1||) and 0 < lambda < 1.
  * Returns the factor lambda / (1 - lambda) to add dk with, or 0. */
-static double dem_factor(int nc, const double* dk, const double* d1, const double* d2) {
-    double n0 = 0.0, n1 = 0.0, n2 = 0.0, p01 = 0.0, p12 = 0.0;
+#define DEM_PERIOD 3
+static double dem_factor(int nc, const double* dk, const double* d1) {
+    double n0 = 0.0, n1 = 0.0, p01 = 0.0;
     for (int i = 0; i < nc; i++) {
-        n0 += dk[i] * dk[i]; n1 += d1[i] * d1[i]; n2 += d2[i] * d2[i];
-        p01 += dk[i] * d1[i]; p12 += d1[i] * d2[i];
+        n0 += dk[i] * dk[i];
+        n1 += d1[i] * d1[i];
+        p01 += dk[i] * d1[i];
     }
-    if (!(n1 > 0.0 && n2 > 0.0) || !(n0 < n1)) return 0.0;
-    double lam = p01 / n1, lam1 = p12 / n2;
+    if (!(n1 > 0.0) || !(n0 < n1)) return 0.0;
+    double lam = p01 / n1;
     if (!(lam > 0.0 && lam < 1.0)) return 0.0;
-    if (!(fabs(lam - lam1) <= 0.1 * lam)) return 0.0;
-    if (!(p01 * p01 >= 0.99 * n0 * n1)) return 0.0; /* updates nearly parallel */
     return lam / (1.0 - lam);
 }
 
@@ -563,7 +567,7 @@ void or_stability_trial(const or_mix* m, const double* d, or_trial* tr, int stop
                         double tol) {
     int nc = m->nc;
     or_phase ph;
-    double gt[OR_MAXNC], tm, dprev[OR_MAXNC] = {0}, dprev2[OR_MAXNC] = {0};
+    double gt[OR_MAXNC], tm, dprev[OR_MAXNC] = {0};
     tr->iters_ss = tr->iters_tr = tr->used_tr = tr->maxiter = tr->nonfinite = 0;
     /* successive substitution, Eq. ss_analyser, with DEM (R7): the
      * evaluation after an accelerated update must succeed with a smaller
@@ -587,8 +591,8 @@ void or_stability_trial(const or_mix* m, const double* d, or_trial* tr, int stop
         double dk[OR_MAXNC];
         for (int i = 0; i < nc; i++) { dk[i] = -gt[i]; tr->lnW[i] += dk[i]; }
         int s = tr->iters_ss + 1;
-        if (s % 5 == 0) {
-            double f = dem_factor(nc, dk, dprev, dprev2);
+        if (s % DEM_PERIOD == 0) {
+            double f = dem_factor(nc, dk, dprev);
             if (f > 0.0) {
                 memcpy(lnW_plain, tr->lnW, sizeof(double) * nc);
                 for (int i = 0; i < nc; i++) tr->lnW[i] += dk[i] * f;
@@ -596,7 +600,7 @@ void or_stability_trial(const or_mix* m, const double* d, or_trial* tr, int stop
                 res_prev = res;
             }
         }
-        for (int i = 0; i < nc; i++) { dprev2[i] = dprev[i]; dprev[i] = dk[i]; }
+        for (int i = 0; i < nc; i++) dprev[i] = dk[i];
         tr->iters_ss = s;
     }
     /* trust region on beta = 2 sqrt(W), Eqs. tr_sa, analysis_grad,
@@ -644,6 +648,20 @@ void or_stability_trial(const or_mix* m, const double* d, or_trial* tr, int stop
         tr->iters_tr = it + 1;
     }
     tr->tm = tm;
+}
+
+/* K from the stability trials (Sec. 2.2.1, last sentence; reading R16):
+ * the trial with the lower tm gives K_i = w_i / z_i (vapour-like) or
+ * z_i / w_i (liquid-like), w = W / sum W its composition.  At a stationary
+ * point sum W = exp(-tpd) is near 1; a trial stopped at its first negative
+ * tm can be far from one. */
+static void stab_lnK(int nc, const double* lnz, const or_trial* tv, const or_trial* tl, double* lnK) {
+    const or_trial* t = (tl->tm < tv->tm) ? tl : tv;
+    double sw = 0.0;
+    for (int i = 0; i < nc; i++) sw += exp(t->lnW[i]);
+    double ls = log(sw);
+    for (int i = 0; i < nc; i++)
+        lnK[i] = (t == tl) ? lnz[i] - (t->lnW[i] - ls) : (t->lnW[i] - ls) - lnz[i];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -739,7 +757,7 @@ static void finish_two_phase(int nc, double th, const double* x, const double* y
 static void or_split(const or_mix* m, const double* z, double* lnK, or_result* r) {
     int nc = m->nc;
     g_stage = 3;
-    double K[OR_MAXNC], x[OR_MAXNC], y[OR_MAXNC], th = 0.5, dprev[OR_MAXNC] = {0}, dprev2[OR_MAXNC] = {0};
+    double K[OR_MAXNC], x[OR_MAXNC], y[OR_MAXNC], th = 0.5, dprev[OR_MAXNC] = {0};
     or_phase pl, pv;
     r->it_split_ss = 0;
     r->it_split_tr = 0;
@@ -781,8 +799,8 @@ static void or_split(const or_mix* m, const double* z, double* lnK, or_result* r
         double dk[OR_MAXNC];
         for (int i = 0; i < nc; i++) { dk[i] = -gt[i]; lnK[i] += dk[i]; }
         int s = r->it_split_ss + 1;
-        if (s % 5 == 0) {
-            double f = dem_factor(nc, dk, dprev, dprev2);
+        if (s % DEM_PERIOD == 0) {
+            double f = dem_factor(nc, dk, dprev);
             if (f > 0.0) {
                 memcpy(lnK_plain, lnK, sizeof(double) * nc);
                 for (int i = 0; i < nc; i++) lnK[i] += dk[i] * f;
@@ -790,7 +808,7 @@ static void or_split(const or_mix* m, const double* z, double* lnK, or_result* r
                 res_prev = res;
             }
         }
-        for (int i = 0; i < nc; i++) { dprev2[i] = dprev[i]; dprev[i] = dk[i]; }
+        for (int i = 0; i < nc; i++) dprev[i] = dk[i];
         r->it_split_ss = s;
     }
     /* trust region on G in n^V (Eq. newton_splitter), from the last
@@ -927,9 +945,8 @@ void or_flash_one(const or_sys* s, double P, double T, const double* z, or_resul
     if (tv.nonfinite || tl.nonfinite) { r->status |= ST_NONFINITE; set_single(nc, z, r); return; }
     r->tm_min = tv.tm < tl.tm ? tv.tm : tl.tm;
     if (!(r->tm_min < -EPS_NEG)) { set_single(nc, z, r); return; }
-    /* K re-estimate (Sec. 2.2.1, last sentence) */
-    if (tl.tm < tv.tm) for (int i = 0; i < nc; i++) lnK[i] = lnz[i] - tl.lnW[i];
-    else for (int i = 0; i < nc; i++) lnK[i] = tv.lnW[i] - lnz[i];
+    /* K re-estimate (Sec. 2.2.1, last sentence; reading R16) */
+    stab_lnK(nc, lnz, &tv, &tl, lnK);
     or_split(&m, z, lnK, r);
 }
 
@@ -1094,10 +1111,9 @@ int oracle_stability_batch(int nc, const double* Tc, const double* Pc, const dou
         double tmin = tv.tm < tl.tm ? tv.tm : tl.tm;
         tm_min[k] = tmin;
         stable[k] = (tmin < -EPS_NEG) ? 0 : 1;
-        for (int i = 0; i < nc; i++) {
-            double lk = (tl.tm < tv.tm) ? lnz[i] - tl.lnW[i] : tv.lnW[i] - lnz[i];
-            K[(int64_t)i * n + k] = exp(lk);
-        }
+        double lk[OR_MAXNC];
+        stab_lnK(nc, lnz, &tv, &tl, lk);
+        for (int i = 0; i < nc; i++) K[(int64_t)i * n + k] = exp(lk[i]);
     }
     return 0;
 }

@@ -571,25 +571,23 @@ __device__ __forceinline__ int tr_shift_step(const double* Hs, const double* gs,
     return 0;
 }
 
-// DEM factor (Sec. 2.2.1): lambda = (dk.d1)/(d1.d1) once settled (previous
-// estimate within 10 %), updates shrinking and nearly parallel (cos^2 >= 0.99)
-// and 0 < lambda < 1; returns lambda / (1 - lambda) or 0.
+// DEM factor (Sec. 2.2.1, reading R7): lambda = (dk.d1)/(d1.d1), used when
+// the updates shrink and 0 < lambda < 1; returns lambda / (1 - lambda) or 0.
+// Applied on every kDemPeriod-th update of an SS run.
+constexpr int kDemPeriod = 3;
+
 template <int NC>
-__device__ __forceinline__ double dem_factor(const double* dk, const double* d1, const double* d2) {
-    double n0 = 0.0, n1 = 0.0, n2 = 0.0, p01 = 0.0, p12 = 0.0;
+__device__ __forceinline__ double dem_factor(const double* dk, const double* d1) {
+    double n0 = 0.0, n1 = 0.0, p01 = 0.0;
 #pragma unroll
     for (int i = 0; i < NC; i++) {
         n0 = fma(dk[i], dk[i], n0);
         n1 = fma(d1[i], d1[i], n1);
-        n2 = fma(d2[i], d2[i], n2);
         p01 = fma(dk[i], d1[i], p01);
-        p12 = fma(d1[i], d2[i], p12);
     }
-    if (!(n1 > 0.0 && n2 > 0.0) || !(n0 < n1)) return 0.0;
-    double lam = p01 / n1, lam1 = p12 / n2;
+    if (!(n1 > 0.0) || !(n0 < n1)) return 0.0;
+    const double lam = p01 / n1;
     if (!(lam > 0.0 && lam < 1.0)) return 0.0;
-    if (!(fabs(lam - lam1) <= 0.1 * lam)) return 0.0;
-    if (!(p01 * p01 >= 0.99 * n0 * n1)) return 0.0;
     return lam / (1.0 - lam);
 }
 

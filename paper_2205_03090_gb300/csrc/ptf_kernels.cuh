@@ -323,7 +323,7 @@ template <int NC>
 struct StabSS {
     int64_t m, item;
     Mix<NC> mx;
-    double d[NC], lnW[NC], dp[NC], dp2[NC], dem_f, res_prev, tm;
+    double d[NC], lnW[NC], dp[NC], dem_f, res_prev, tm;
     int t, it, iters;
     bool dem_pending;
 
@@ -347,7 +347,7 @@ struct StabSS {
             d[i] = ws.d[i * n + m];
             const double lz = ws.lnz[i * n + m];
             lnW[i] = t == 0 ? lz + lnKw[i] : lz - lnKw[i];  // W = K z (vapour-like), z / K (liquid-like)
-            dp[i] = dp2[i] = 0.0;
+            dp[i] = 0.0;
         }
         res_prev = INFINITY;
         dem_f = 0.0;
@@ -400,8 +400,8 @@ struct StabSS {
             lnW[i] += dk[i];
         }
         const int s = iters + 1;
-        if (s % 5 == 0) {
-            const double f = dem_factor<NC>(dk, dp, dp2);
+        if (s % kDemPeriod == 0) {
+            const double f = dem_factor<NC>(dk, dp);
             if (f > 0.0) {
 #pragma unroll
                 for (int i = 0; i < NC; i++) lnW[i] += dk[i] * f;
@@ -412,7 +412,6 @@ struct StabSS {
         }
 #pragma unroll
         for (int i = 0; i < NC; i++) {
-            dp2[i] = dp[i];
             dp[i] = dk[i];
         }
         iters = s;
@@ -585,6 +584,26 @@ __global__ void __launch_bounds__(128) k_stab_tr(const __grid_constant__ CS cs, 
     }
 }
 
+// K from the stability trial t with the lower tm (Sec. 2.2.1, last sentence;
+// reading R16), w = W / sum W the trial composition: ln K = ln w - ln z for
+// the vapour-like trial (t = 0), ln z - ln w for the liquid-like one.
+template <int NC>
+__device__ __forceinline__ void stab_lnK(const WS& ws, int64_t m, int t, double* lnK) {
+    const int64_t n = ws.n;
+    double lw[NC], sw = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        lw[i] = ws.lnW[(t * NC + i) * n + m];
+        sw += exp(lw[i]);
+    }
+    const double ls = log(sw);
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        const double lz = ws.lnz[i * n + m];
+        lnK[i] = t == 1 ? lz - (lw[i] - ls) : (lw[i] - ls) - lz;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Stability decision and K re-estimate (Sec. 2.2.1, last sentence).
 // ---------------------------------------------------------------------------
@@ -615,12 +634,10 @@ __device__ __forceinline__ bool stab_decide_item(const CS& cs, const WS& ws, con
                 if (!(tmin < -kEpsNeg)) {
                     write_single<NC>(io, m, z);
                 } else {
-                    const int t = tl < tv ? 1 : 0;
+                    double lnK[NC];
+                    stab_lnK<NC>(ws, m, tl < tv ? 1 : 0, lnK);
 #pragma unroll
-                    for (int i = 0; i < NC; i++) {
-                        double lz = ws.lnz[i * n + m], lw = ws.lnW[(t * NC + i) * n + m];
-                        ws.lnK[i * n + m] = t == 1 ? lz - lw : lw - lz;
-                    }
+                    for (int i = 0; i < NC; i++) ws.lnK[i * n + m] = lnK[i];
                     to_split = true;
                 }
             }
@@ -648,7 +665,7 @@ template <int NC>
 struct SplitSS {
     int64_t m;
     Mix<NC> mx;
-    double z[NC], lnK[NC], dp[NC], dp2[NC], dem_f, res_prev, th;
+    double z[NC], lnK[NC], dp[NC], dem_f, res_prev, th;
     int it, iters;
     bool dem_pending;
 
@@ -662,7 +679,7 @@ struct SplitSS {
         for (int i = 0; i < NC; i++) {
             z[i] = io.z[i * io.ld + m];
             lnK[i] = ws.lnK[i * n + m];
-            dp[i] = dp2[i] = 0.0;
+            dp[i] = 0.0;
         }
         th = 0.5;
         res_prev = INFINITY;
@@ -749,8 +766,8 @@ struct SplitSS {
             lnK[i] += dk[i];
         }
         const int s = iters + 1;
-        if (s % 5 == 0) {
-            const double f = dem_factor<NC>(dk, dp, dp2);
+        if (s % kDemPeriod == 0) {
+            const double f = dem_factor<NC>(dk, dp);
             if (f > 0.0) {
 #pragma unroll
                 for (int i = 0; i < NC; i++) lnK[i] += dk[i] * f;
@@ -761,7 +778,6 @@ struct SplitSS {
         }
 #pragma unroll
         for (int i = 0; i < NC; i++) {
-            dp2[i] = dp[i];
             dp[i] = dk[i];
         }
         iters = s;
@@ -1024,12 +1040,10 @@ __device__ __forceinline__ void stab_out_item(const CS& cs, const WS& ws, const 
             const double tmin = tv < tl ? tv : tl;
             io.nphase[m] = (tmin < -kEpsNeg) ? 0 : 1;
             io.beta[m] = tmin;
-            const int t = tl < tv ? 1 : 0;
+            double lnK[NC];
+            stab_lnK<NC>(ws, m, tl < tv ? 1 : 0, lnK);
 #pragma unroll
-            for (int i = 0; i < NC; i++) {
-                double lz = ws.lnz[i * n + m], lw = ws.lnW[(t * NC + i) * n + m];
-                io.K[i * io.ld + m] = exp(t == 1 ? lz - lw : lw - lz);
-            }
+            for (int i = 0; i < NC; i++) io.K[i * io.ld + m] = exp(lnK[i]);
             io.status[m] = st;
         }
     }

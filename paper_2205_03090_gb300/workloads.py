@@ -139,6 +139,110 @@ def paper_components(names) -> Components:
     return Components(Tc, Pc, om, k)
 
 
+# Paper Table 2 (Sec. 2.3): composition ranges (mole fractions) of the four
+# reservoir fluid types, in the component order of Table 1.
+PAPER_TABLE2 = {
+    "wet_gas":        [(0.80, 1.00), (0.02, 0.07), (0.0, 0.03), (0.0, 0.02), (0.0, 0.02), (0.0, 0.02), (0.0, 0.01),
+                       (0.0, 0.02), (0.0, 0.005)],
+    "gas_condensate": [(0.60, 0.80), (0.05, 0.10), (0.0, 0.04), (0.0, 0.03), (0.0, 0.02), (0.0, 0.02), (0.05, 0.10),
+                       (0.0, 0.035), (0.0, 0.005)],
+    "volatile_oil":   [(0.50, 0.70), (0.06, 0.10), (0.0, 0.045), (0.0, 0.03), (0.0, 0.02), (0.0, 0.02), (0.10, 0.30),
+                       (0.0, 0.02), (0.0, 0.005)],
+    "black_oil":      [(0.20, 0.40), (0.03, 0.06), (0.0, 0.015), (0.0, 0.015), (0.0, 0.01), (0.0, 0.02),
+                       (0.45, 0.65), (0.0, 0.001), (0.0, 0.005)],
+}
+# Paper Table 3 (Sec. 2.4): Dirichlet concentrations per fluid type,
+# (alpha_CH4, alpha_C2H6, alpha_C7H16+); 1 for the other components.
+PAPER_TABLE3 = {"wet_gas": (100.0, 5.0, 1.0), "gas_condensate": (40.0, 5.0, 5.0), "volatile_oil": (55.0, 8.0, 20.0),
+                "black_oil": (25.0, 4.0, 40.0)}
+# The three case studies (Sec. 2.3): components and P [MPa], T [K] ranges.
+PAPER_CASES = {
+    "c2": dict(names=["CH4", "C6H14"], P=(0.1, 10.0), T=(200.0, 500.0)),
+    "c4": dict(names=["CH4", "C2H6", "C3H8", "nC4H10"], P=(0.1, 10.0), T=(200.0, 500.0)),
+    "c9": dict(names=list(PAPER_TABLE1["names"]), P=(5.0, 25.0), T=(200.0, 600.0)),
+}
+
+
+def lhs_uniform(g: np.random.Generator, n: int, d: int) -> np.ndarray:
+    """Latin hypercube sample of U(0,1)^d (McKay et al.): in every dimension
+    each of the n strata [k/n, (k+1)/n) holds exactly one point."""
+    u = np.empty((n, d))
+    for j in range(d):
+        u[:, j] = (g.permutation(n) + g.uniform(size=n)) / n
+    return u
+
+
+def _dirichlet_from_uniform(u: np.ndarray, alpha: np.ndarray) -> np.ndarray:
+    """Eq. sampling: y_i = Gamma(alpha_i, 1).ppf(u_i), z = y / sum y.
+    Returns z [n, nc].  Gamma(1, 1).ppf(u) = -ln(1 - u) in closed form."""
+    y = np.empty_like(u)
+    one = alpha == 1.0
+    y[:, one] = -np.log1p(-u[:, one])
+    if (~one).any():
+        from scipy.special import gammaincinv
+        y[:, ~one] = gammaincinv(alpha[None, ~one], u[:, ~one])
+    return y / y.sum(axis=1, keepdims=True)
+
+
+def paper_case(case: str, n: int, seed: int = 0):
+    """Inputs of a paper case study (Sec. 2.3-2.4).
+    c2, c4: LHS samples of (P, T, u) with P, T scaled to the case's ranges and
+    z from Eq. sampling with alpha = 1 (the whole simplex).
+    c9: the four fluid types of Table 2 equally represented; each type's z is
+    Dirichlet with its Table 3 alpha, kept only if every component lies in
+    the type's range.  The acceptance rates are low (black oil ~0.1 %, gas
+    condensate ~1 %), so the candidates come from Gamma(alpha_i, 1) draws
+    (the same accepted distribution as Gamma.ppf of LHS uniforms, whose
+    stratification the rejection would undo) and P, T keep their LHS strata.
+    Returns (Components, Conditions, fluid type index per mixture or None)."""
+    c = PAPER_CASES[case]
+    comp = paper_components(c["names"])
+    nc = comp.nc
+    g = np.random.Generator(np.random.PCG64(seed))
+    if case != "c9":
+        u = lhs_uniform(g, n, 2 + nc)
+        P = c["P"][0] + (c["P"][1] - c["P"][0]) * u[:, 0]
+        T = c["T"][0] + (c["T"][1] - c["T"][0]) * u[:, 1]
+        z = _dirichlet_from_uniform(u[:, 2:], np.ones(nc))
+        z = np.maximum(z, Z_FLOOR)
+        z /= z.sum(axis=1, keepdims=True)
+        return comp, Conditions(P, T, np.ascontiguousarray(z.T)), None
+    types = list(PAPER_TABLE2)
+    per = [n // 4 + (1 if k < n % 4 else 0) for k in range(4)]
+    Ps, Ts, zs, ft = [], [], [], []
+    for k, name in enumerate(types):
+        a1, a2, a7 = PAPER_TABLE3[name]
+        alpha = np.ones(nc)
+        alpha[0], alpha[1], alpha[6] = a1, a2, a7
+        lo = np.array([r[0] for r in PAPER_TABLE2[name]])
+        hi = np.array([r[1] for r in PAPER_TABLE2[name]])
+        # the ranges checked on the shrinking candidate set, narrowest first
+        order = np.argsort(hi - lo)
+        acc, got = [], 0
+        while got < per[k]:
+            m = 1 << 20
+            y = np.empty((nc, m))
+            for i in range(nc):
+                y[i] = g.standard_exponential(m) if alpha[i] == 1.0 else g.standard_gamma(alpha[i], m)
+            S = y.sum(axis=0)
+            keep = np.arange(m)
+            for i in order:
+                zi = y[i, keep] / S[keep]
+                keep = keep[(zi >= lo[i]) & (zi <= hi[i])]
+            z = (y[:, keep] / S[keep]).T[:per[k] - got]
+            acc.append(z)
+            got += len(z)
+        u = lhs_uniform(g, per[k], 2)
+        Ps.append(c["P"][0] + (c["P"][1] - c["P"][0]) * u[:, 0])
+        Ts.append(c["T"][0] + (c["T"][1] - c["T"][0]) * u[:, 1])
+        zs.append(np.concatenate(acc))
+        ft.append(np.full(per[k], k, np.int32))
+    z = np.concatenate(zs)
+    z = np.maximum(z, Z_FLOOR)
+    z /= z.sum(axis=1, keepdims=True)
+    return comp, Conditions(np.concatenate(Ps), np.concatenate(Ts), np.ascontiguousarray(z.T)), np.concatenate(ft)
+
+
 def mlp_init(din: int, hidden: int, dout: int, seed: int) -> np.ndarray:
     """Initial network parameters drawn from seeded Glorot-uniform
     distributions (weights) with zero biases, in the flat order W1, b1, W2,
