@@ -272,6 +272,69 @@ def cases_leg(args, rank, dev, flush, stream):
     return out_all
 
 
+# Paper Table 5 (NN-PTFlash, 9 components, 1e6 mixtures, RTX 3080); context only.
+PAPER_TABLE5 = {"classifier_decided_frac": 0.9942, "stab": 5818, "split": 413442, "split_ss_converged_frac": 0.674,
+                "split_tr": 134786, "speedup_vs_plain_gpu": 2.2}
+
+
+def paper_learned_leg(args, rank, dev, flush, stream):
+    """The paper's networks (classifier 3 x 32, residual + wide initializer)
+    on the 9-component case study: plain vs learned form on the same 1e6
+    mixtures, stage counts beside Table 5, sampled oracle check.  Trains the
+    networks first if the checkpoint is missing."""
+    import torch
+    from paper_2205_03090_gb300 import nn, ptflash, workloads as wl
+    from paper_2205_03090_gb300 import train_paper_nn
+    if not nn.exists(train_paper_nn.DEFAULT_OUT):
+        train_paper_nn.main([])
+    n = max(1, int(1_000_000 * args.cases_scale))
+    comp, cond, ft = wl.paper_case("c9", n, 300 + rank)
+    fl = ptflash.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=n)
+    meta = nn.load_checkpoint(fl, train_paper_nn.DEFAULT_OUT)
+    P = torch.tensor(cond.P, device=dev)
+    T = torch.tensor(cond.T, device=dev)
+    z = torch.tensor(cond.z, device=dev).contiguous()
+    out = fl.alloc_outputs(n, dev)
+    res = {}
+    for form in ("plain", "learned"):
+        use = form == "learned"
+        ms = []
+        for it in range(args.warmup + max(1, args.steps)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fl.ptflash_flash(P, T, z, out=out, use_nn=use, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                ms.append(e0.elapsed_time(e1))
+        q = fl.ptflash_last_counts()
+        st = out.status.cpu().numpy()
+        res[form] = {"ms_per_step": float(np.mean(ms)), "queues": q,
+                     "split_ss_converged_frac": 1.0 - q["split_tr"] / max(1, q["split"])}
+        if use:
+            res[form]["classifier_decided_frac"] = float(((st & (128 | 256)) != 0).mean())
+            g = {k: getattr(out, k).cpu().numpy() for k in ("nphase", "beta", "x", "y", "status")}
+    frac, sample = float("nan"), 0
+    if rank == 0 and args.cpu_sample > 0:
+        rng = np.random.default_rng(31)
+        sample = min(n, 20000)
+        idx = np.sort(rng.choice(n, sample, replace=False))
+        o, _, s = run_oracle_sample(comp, cond, idx)
+        frac = match_fraction(s, comp, cond, idx, o, g)
+    fl.close()
+    lv = n * (frac if frac == frac else 1.0) / (res["learned"]["ms_per_step"] / 1e3)
+    return {"workload": "paper case study, 9 components, four fluid types, 1e6 mixtures", "n": n,
+            "value": lv, "unit": "flashes/s", "ms_per_step": res["learned"]["ms_per_step"],
+            "plain_ms_per_step": res["plain"]["ms_per_step"],
+            "speedup_vs_plain": res["plain"]["ms_per_step"] / res["learned"]["ms_per_step"],
+            "oracle_match": {"frac": frac, "sample": sample, "tol": TOL}, "plain": res["plain"],
+            "learned": res["learned"], "networks": {k: meta.get(k) for k in ("classifier", "initializer")},
+            "paper_table5_context": PAPER_TABLE5}
+
+
 def run_oracle_sample(comp, cond, idx, nthreads=None):
     import oracle
     s = oracle.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
@@ -419,6 +482,7 @@ def ours_arm(args, ws, rank, local):
     uneven = uneven_leg(args, rank, dev, flush, stream) if args.uneven else None
     adjoint = adjoint_leg(args, rank, dev, flush, stream) if args.adjoint else None
     cases = cases_leg(args, rank, dev, flush, stream) if args.cases else None
+    paper_learned = paper_learned_leg(args, rank, dev, flush, stream) if args.paper_nn else None
 
     if rank != 0:
         if dist:
@@ -474,6 +538,7 @@ def ours_arm(args, ws, rank, local):
         "uneven": uneven,
         "adjoint": adjoint,
         "paper_cases": cases,
+        "paper_learned": paper_learned,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -555,6 +620,7 @@ def main():
     ap.add_argument("--adjoint", type=int, default=1, help="run the flash + adjoint leg (0 skips it)")
     ap.add_argument("--cases", type=int, default=1, help="run the paper case-study leg (0 skips it)")
     ap.add_argument("--cases-scale", type=float, default=1.0, help="fraction of the case-study batch sizes")
+    ap.add_argument("--paper-nn", type=int, default=1, help="run the paper-network leg on the 9-component case")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

@@ -243,18 +243,28 @@ int ptflash_batch_tune(ptflash_batch* b, const double* P, const double* T, const
 int ptflash_batch_info(const ptflash_batch* b, int32_t* ngroups, int64_t* graph_nodes, int64_t* mixtures);
 
 /*
- * Learned form (Sec. 4 of the paper).  which = 0: stability classifier
- * (3 hidden layers of `hidden` SiLU units, one logit; p = sigmoid(logit) is
- * the probability that the mixture is stable); which = 1: ln K initializer
- * (3 hidden layers of `hidden` SiLU units, nc outputs).  Inputs are the nc + 2
- * features (z_1..z_nc, P, T), standardised as (v - mean) / std (the paper's
- * scaling layer) and rounded to bfloat16; weights and hidden activations are
- * bfloat16, sums FP32.  Parameters: one FP32 vector W1, b1, W2, b2, W3, b3,
- * W4, b4 with each W row-major [out][in] (count: ptflash_nn_param_count(nc + 2,
- * hidden, dout)).  hidden must be 64 or 128.
+ * Learned form (Sec. 4 of the paper).  which = 0: stability classifier (one
+ * logit; p = sigmoid(logit) is the probability that the mixture is stable);
+ * which = 1: ln K initializer (nc outputs).  Inputs are the nc + 2 features
+ * (z_1..z_nc, P, T), standardised as (v - mean) / std (the paper's scaling
+ * layer) and rounded to bfloat16; weights and hidden activations are
+ * bfloat16, sums FP32, SiLU hidden units.  Two architectures:
+ *   arch 0: 3 hidden layers of `hidden` units (32, 64 or 128; the paper's
+ *     classifier is 3 x 32, Sec. 4.1.1);
+ *   arch 1: the paper's initializer (Sec. 4.2.1): a hidden layer, 3 residual
+ *     blocks of 2 hidden layers (h <- h + block(h)), all `hidden` units (32
+ *     or 64), and a linear output on the concatenation [inputs; h].
+ * Parameters: one FP32 vector W_0, b_0, W_1, b_1, ... with each W row-major
+ * [out][in] (count: ptflash_nn_param_count_arch(arch, nc + 2, hidden, dout)).
  *
- * ptflash_nn_set: HOST theta, mean[nc+2], std[nc+2]; copies them, makes the
- *   bfloat16 compute copy and resets the Adam state.  Components must be set.
+ * ptflash_nn_set_arch: HOST theta, mean[nc+2], std[nc+2]; copies them, makes
+ *   the bfloat16 compute copy and resets the Adam state.  Components must be
+ *   set.  ptflash_nn_set is arch 0.
+ * ptflash_nn_set_theta_loss (initializer only): weight w >= 0 of the second
+ *   training stage's |theta - theta_hat| term (Sec. 4.2.2; 0 turns it off).
+ *   theta_hat is the Rachford-Rice root for the predicted K, solved in FP64,
+ *   and its gradient comes from the implicit-function theorem.  With w > 0
+ *   the initializer's targets Y carry 2 nc + 1 rows: ln K, theta, raw z.
  * ptflash_nn_get: copies the FP32 parameters to HOST theta (synchronises).
  * ptflash_nn_features: DEVICE X[(nc+2) * n] (row stride n), the standardised
  *   bfloat16 features of DEVICE P, T, z.
@@ -263,13 +273,19 @@ int ptflash_batch_info(const ptflash_batch* b, int32_t* ngroups, int64_t* graph_
  *   of `batch` samples each (a multiple of 128).  DEVICE X[(nc+2) * n]
  *   features, Y targets (classifier: [n], 1 stable / 0 unstable, binary
  *   cross-entropy on the logit; initializer: [nc * n] ln K, absolute error
- *   summed over components; both averaged over the batch), perm[steps *
- *   batch] sample indices, HOST lr[steps] learning rates, optional DEVICE
- *   loss[steps] (each entry incremented by that step's batch loss; zero it
- *   first).  The first call allocates training scratch.
- * ptflash_nn_eval: mean loss and (classifier) accuracy at p = 1/2 over DEVICE
- *   X[(nc+2) * n], Y (same layouts); synchronises.
+ *   summed over components, plus the theta term when set; all averaged over
+ *   the batch), perm[steps * batch] sample indices, HOST lr[steps] learning
+ *   rates, optional DEVICE loss[steps] (each entry incremented by that step's
+ *   batch loss; zero it first).  The first call allocates training scratch.
+ * ptflash_nn_eval: mean loss over DEVICE X[(nc+2) * n], Y (same layouts), and
+ *   in *accuracy the classifier's accuracy at p = 1/2, or for the
+ *   initializer with the theta term the mean |theta - theta_hat| (else 0);
+ *   synchronises.
  */
+int64_t ptflash_nn_param_count_arch(int arch, int din, int hidden, int dout);
+int ptflash_nn_set_arch(ptflash_ctx* ctx, int which, int arch, int hidden, const float* theta, const float* mean,
+                        const float* std);
+int ptflash_nn_set_theta_loss(ptflash_ctx* ctx, int which, float weight);
 int64_t ptflash_nn_param_count(int din, int hidden, int dout);
 int ptflash_nn_set(ptflash_ctx* ctx, int which, int hidden, const float* theta, const float* mean, const float* std);
 int ptflash_nn_get(ptflash_ctx* ctx, int which, float* theta);

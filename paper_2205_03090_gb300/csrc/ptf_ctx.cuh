@@ -19,8 +19,10 @@ struct NNState {
     float* adam_v = nullptr;
     long long t = 0;                 // Adam step count
     bool ready = false;
+    int arch = 0;                    // 0: three hidden layers; 1: residual blocks + wide output
+    float theta_w = 0.0f;            // initializer: weight of |theta - theta_hat| in the loss (0: off)
 
-    MLP view() const { return MLP{din, hid, dout, theta, wt, mean, rstd}; }
+    MLP view() const { return MLP{din, hid, dout, theta, wt, mean, rstd, arch}; }
 };
 }  // namespace ptf
 

@@ -1,14 +1,21 @@
 // ptf_mlp.cuh -- the two networks of the learned form (Sec. 4): BF16
 // weights and activations, FP32 accumulation, SiLU hidden layers.
 //
-// Network: inputs u = bf16((v - mean) * rstd), v = (z_1..z_nc, P, T) (the
-// scaling layer, Sec. 4.1.1); three hidden layers a_l = bf16(silu(W_l a_{l-1}
-// + b_l)); linear output.  Classifier: H = 64, one logit (p = sigmoid, the
-// probability of a stable mixture).  Initializer: H = 128, nc outputs (ln K).
+// Inputs u = bf16((v - mean) * rstd), v = (z_1..z_nc, P, T) (the scaling
+// layer, Sec. 4.1.1).  Two architectures:
+//  - arch 0: three hidden layers a_l = bf16(silu(W_l a_{l-1} + b_l)) and a
+//    linear output (the classifier of Sec. 4.1.1 has 3 x 32 units; widths 64
+//    and 128 are the larger variants used elsewhere);
+//  - arch 1 (the initializer of Sec. 4.2.1): h_0 = bf16(silu(W_0 u + b_0)),
+//    three residual blocks h_k = bf16(h_{k-1} + silu(W_{2k} silu(W_{2k-1}
+//    h_{k-1} + b) + b)) (every activation bf16), and a linear output on the
+//    concatenation [u; h_3] (the wide shortcut).
+// Layers: arch 0 has 4 (din->H, H->H, H->H, H->dout); arch 1 has 8
+// (din->H, six H->H, din+H->dout).
 //
 // Parameter storage:
-//  - theta: FP32 master vector, natural layout W1 [H x din], b1, W2 [H x H],
-//    b2, W3, b3, W4 [dout x H], b4 (row-major [out, in]);
+//  - theta: FP32 master vector, W_0, b_0, W_1, b_1, ... (each W row-major
+//    [out, in]);
 //  - wt: BF16 compute copy of the weights, each layer transposed [in][out]
 //    and padded to a multiple of 8 outputs, so one 16-byte load fetches 8
 //    consecutive outputs of one input.
@@ -26,11 +33,15 @@ struct MLP {
     const __nv_bfloat16* wt;     // BF16 transposed, padded
     const float* mean;           // [din] feature means
     const float* rstd;           // [din] 1 / feature standard deviations
+    int arch = 0;                // 0: three hidden layers; 1: residual blocks + wide output
 };
 
 __host__ __device__ inline int pad8(int x) { return (x + 7) & ~7; }
-__host__ __device__ inline int layer_in(const MLP& a, int l) { return l == 0 ? a.din : a.hid; }
-__host__ __device__ inline int layer_out(const MLP& a, int l) { return l == 3 ? a.dout : a.hid; }
+__host__ __device__ inline int n_layers(const MLP& a) { return a.arch ? 8 : 4; }
+__host__ __device__ inline int layer_in(const MLP& a, int l) {
+    return l == 0 ? a.din : (a.arch && l == 7 ? a.din + a.hid : a.hid);
+}
+__host__ __device__ inline int layer_out(const MLP& a, int l) { return l == n_layers(a) - 1 ? a.dout : a.hid; }
 // offsets of W_l and b_l in theta
 __host__ __device__ inline int64_t theta_W(const MLP& a, int l) {
     int64_t o = 0;
@@ -40,18 +51,14 @@ __host__ __device__ inline int64_t theta_W(const MLP& a, int l) {
 __host__ __device__ inline int64_t theta_b(const MLP& a, int l) {
     return theta_W(a, l) + (int64_t)layer_out(a, l) * layer_in(a, l);
 }
-__host__ __device__ inline int64_t theta_size(int din, int hid, int dout) {
-    return (int64_t)hid * din + hid + 2 * ((int64_t)hid * hid + hid) + (int64_t)dout * hid + dout;
-}
+__host__ __device__ inline int64_t theta_size(const MLP& a) { return theta_W(a, n_layers(a)); }
 // offset of layer l in wt ([in][pad8(out)])
 __host__ __device__ inline int64_t wt_off(const MLP& a, int l) {
     int64_t o = 0;
     for (int k = 0; k < l; k++) o += (int64_t)layer_in(a, k) * pad8(layer_out(a, k));
     return o;
 }
-__host__ __device__ inline int64_t wt_size(int din, int hid, int dout) {
-    return (int64_t)din * pad8(hid) + 2 * (int64_t)hid * pad8(hid) + (int64_t)hid * pad8(dout);
-}
+__host__ __device__ inline int64_t wt_size(const MLP& a) { return wt_off(a, n_layers(a)); }
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + __expf(-x)); }
@@ -110,6 +117,30 @@ __device__ __forceinline__ void features(const MLP& a, int nc, int64_t ld, const
         const double v = i < nc ? z[i * ld + m] : (i == nc ? P[m] : T[m]);
         u[i * st] = bf16_round(((float)v - __ldg(a.mean + i)) * __ldg(a.rstd + i));
     }
+}
+
+// Forward pass of one sample, activations in a column of stride st with
+// rows [u (din)][h (hid)][t1 (hid)][t2 (hid)]; u filled by the caller (arch 1
+// reads [u; h] as the output layer's input).  Output to out (stride out_st).
+__device__ __forceinline__ void forward_sample(const MLP& a, float* col, int64_t st, float* out, int64_t out_st) {
+    float* u = col;
+    float* h = col + a.din * st;
+    float* t1 = h + a.hid * st;
+    float* t2 = t1 + a.hid * st;
+    if (a.arch == 0) {
+        layer_sample<true>(a, 0, u, st, h, st, nullptr, 0);
+        layer_sample<true>(a, 1, h, st, t1, st, nullptr, 0);
+        layer_sample<true>(a, 2, t1, st, h, st, nullptr, 0);
+        layer_sample<false>(a, 3, h, st, out, out_st, nullptr, 0);
+        return;
+    }
+    layer_sample<true>(a, 0, u, st, h, st, nullptr, 0);
+    for (int k = 1; k <= 3; k++) {
+        layer_sample<true>(a, 2 * k - 1, h, st, t1, st, nullptr, 0);
+        layer_sample<true>(a, 2 * k, t1, st, t2, st, nullptr, 0);
+        for (int j = 0; j < a.hid; j++) h[j * st] = bf16_round(h[j * st] + t2[j * st]);
+    }
+    layer_sample<false>(a, 7, u, st, out, out_st, nullptr, 0);
 }
 
 // Network inference over n mixtures (defined in ptf_nn.cu): out[o * out_ld + m].

@@ -26,7 +26,8 @@ int fail(cudaError_t e) {
 
 constexpr int kTile = 128;  // samples per block (one per thread)
 
-size_t infer_smem(const MLP& a) { return (size_t)(kMlpMaxIn + 2 * a.hid) * kTile * sizeof(float); }
+int infer_rows(const MLP& a) { return a.din + (a.arch ? 3 : 2) * a.hid; }
+size_t infer_smem(const MLP& a) { return (size_t)infer_rows(a) * kTile * sizeof(float); }
 
 // Inference: each thread runs its sample through the network, keeping the
 // activations in its own shared-memory column (no cross-thread traffic).
@@ -34,17 +35,12 @@ __global__ void __launch_bounds__(kTile) k_nn_infer(MLP a, int nc, int64_t n, in
                                                     const double* T, const double* z, float* out, int64_t out_ld) {
     extern __shared__ float sm[];
     const int s = threadIdx.x;
-    float* u = sm + s;
-    float* h0 = sm + kMlpMaxIn * kTile + s;
-    float* h1 = h0 + a.hid * kTile;
+    float* col = sm + s;
     for (int64_t base = (int64_t)blockIdx.x * kTile; base < n; base += (int64_t)gridDim.x * kTile) {
         const int64_t m = base + s;
         if (m >= n) continue;
-        features(a, nc, ld, P, T, z, m, u, kTile);
-        layer_sample<true>(a, 0, u, kTile, h0, kTile, nullptr, 0);
-        layer_sample<true>(a, 1, h0, kTile, h1, kTile, nullptr, 0);
-        layer_sample<true>(a, 2, h1, kTile, h0, kTile, nullptr, 0);
-        layer_sample<false>(a, 3, h0, kTile, out + m, out_ld, nullptr, 0);
+        features(a, nc, ld, P, T, z, m, col, kTile);
+        forward_sample(a, col, kTile, out + m, out_ld);
     }
 }
 
@@ -61,93 +57,224 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-size_t train_block_floats(const MLP& a) { return (size_t)(kMlpMaxIn + 8 * a.hid) * kTile; }
+// Vapour fraction of z with K by Rachford-Rice (Eq. RR) on the
+// Leibovici-Neoschil window (Appendix C), bisection with Newton steps inside
+// the bracket, FP64; and its implicit-function-theorem derivative
+// d theta / d ln K_i = K_i z_i / t_i^2 / sum_j z_j (K_j - 1)^2 / t_j^2,
+// t_i = 1 + (K_i - 1) theta (Sec. 4.2.2).  False if K does not bracket 1.
+__device__ bool rr_theta(int nc, const double* z, const double* K, double& th, double* dth) {
+    double kmax = K[0], kmin = K[0];
+    for (int i = 1; i < nc; i++) {
+        kmax = fmax(kmax, K[i]);
+        kmin = fmin(kmin, K[i]);
+    }
+    if (!(kmax > 1.0 && kmin < 1.0)) return false;
+    double lo = 1.0 / (1.0 - kmax), hi = 1.0 / (1.0 - kmin);
+    double t = 0.5 * (lo + hi);
+    for (int it = 0; it < 100; it++) {
+        double f = 0.0, fp = 0.0;
+        for (int i = 0; i < nc; i++) {
+            const double km = K[i] - 1.0, ti = 1.0 / fma(km, t, 1.0);
+            f = fma(z[i] * km, ti, f);
+            fp = fma(-z[i] * km * km, ti * ti, fp);
+        }
+        if (f > 0.0) lo = t; else hi = t;
+        double tn = t - f / fp;
+        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+        const bool done = fabs(tn - t) <= 1e-14 * fmax(1.0, fabs(t));
+        t = tn;
+        if (done || !(hi > lo)) break;
+    }
+    double den = 0.0;
+    for (int i = 0; i < nc; i++) {
+        const double km = K[i] - 1.0, ti = 1.0 / fma(km, t, 1.0);
+        den = fma(z[i] * km * km, ti * ti, den);
+    }
+    for (int i = 0; i < nc; i++) {
+        const double ti = 1.0 / fma(K[i] - 1.0, t, 1.0);
+        dth[i] = K[i] * z[i] * ti * ti / den;
+    }
+    th = t;
+    return true;
+}
 
-// One training step on a batch (kTile samples per block): forward with the
-// activations and silu' kept in the block's scratch, loss (kind 0: binary
-// cross-entropy on the logit, Sec. 4.1.1; kind 1: absolute error of ln K
-// summed over components, Sec. 4.2.1; both averaged over the batch),
-// backward, and the weight / bias gradients summed over the block's samples
-// and added to `grad`.
-__global__ void __launch_bounds__(kTile) k_nn_train_step(MLP a, int kind, int64_t ld, const float* X, const float* Y,
-                                                         const int32_t* perm, int batch, float* grad,
-                                                         float* scratch, float* loss_acc) {
-    const int s = threadIdx.x, lane = s & 31, warp = s >> 5, H = a.hid;
-    float* base = scratch + (size_t)blockIdx.x * ((size_t)(kMlpMaxIn + 8 * H) * kTile);
-    float* u = base;                           // [din][kTile]
-    float* act = u + kMlpMaxIn * kTile;        // [3][H][kTile]
-    float* dsl = act + 3 * H * kTile;          // [3][H][kTile]
-    float* bufA = dsl + 3 * H * kTile;         // [H][kTile]
-    float* bufB = bufA + H * kTile;            // [H][kTile]
-    const int64_t idx = perm[(int64_t)blockIdx.x * kTile + s];
-    for (int i = 0; i < a.din; i++) u[i * kTile + s] = X[i * ld + idx];
-    layer_sample<true>(a, 0, u + s, kTile, act + s, kTile, dsl + s, kTile);
-    layer_sample<true>(a, 1, act + s, kTile, act + H * kTile + s, kTile, dsl + H * kTile + s, kTile);
-    layer_sample<true>(a, 2, act + H * kTile + s, kTile, act + 2 * H * kTile + s, kTile, dsl + 2 * H * kTile + s,
-                       kTile);
-    float outv[16];
-    layer_sample<false>(a, 3, act + 2 * H * kTile + s, kTile, outv, 1, nullptr, 0);
-    const float inv_b = 1.0f / (float)batch;
+// Loss kinds: 0 binary cross-entropy on the logit (classifier, Sec. 4.1.1);
+// 1 absolute error of ln K summed over components (initializer, Sec. 4.2.1);
+// 2 kind 1 plus wth |theta - theta_hat|, theta_hat the Rachford-Rice root
+// for the predicted K (Sec. 4.2.2, second stage).  Kind 2 targets Y carry
+// 2 nc + 1 rows: ln K, theta, then the raw z.
+// Per-sample loss and, with g != null, d loss / d output into g[o * gst].
+__device__ float sample_loss(int kind, int dout, float wth, const float* outv, const float* Y, int64_t ld, int64_t idx,
+                             float scale, float* g, int gst, float* th_err) {
     float l = 0.0f;
+    if (th_err) *th_err = 0.0f;
     if (kind == 0) {
         const float zz = outv[0], y = Y[idx];
         l = fmaxf(zz, 0.0f) + log1pf(__expf(-fabsf(zz))) - y * zz;  // softplus(z) - y z
-        bufA[s] = (sigmoidf_(zz) - y) * inv_b;
-    } else {
-        for (int o = 0; o < a.dout; o++) {
-            const float d = outv[o] - Y[o * ld + idx];
-            l += fabsf(d);
-            bufA[o * kTile + s] = (d > 0.0f ? inv_b : (d < 0.0f ? -inv_b : 0.0f));
+        if (g) g[0] = (sigmoidf_(zz) - y) * scale;
+        return l;
+    }
+    for (int o = 0; o < dout; o++) {
+        const float d = outv[o] - Y[o * ld + idx];
+        l += fabsf(d);
+        if (g) g[o * gst] = (d > 0.0f ? scale : (d < 0.0f ? -scale : 0.0f));
+    }
+    if (kind == 2) {
+        double z[16], K[16], dth[16], th;
+        for (int i = 0; i < dout; i++) {
+            z[i] = (double)Y[(dout + 1 + i) * ld + idx];
+            K[i] = exp((double)outv[i]);
         }
+        if (rr_theta(dout, z, K, th, dth)) {
+            const double e = th - (double)Y[dout * ld + idx];
+            l += wth * (float)fabs(e);
+            if (th_err) *th_err = (float)fabs(e);
+            if (g) {
+                const float sg = e > 0.0 ? scale * wth : (e < 0.0 ? -scale * wth : 0.0f);
+                for (int i = 0; i < dout; i++) g[i * gst] += sg * (float)dth[i];
+            }
+        }
+    }
+    return l;
+}
+
+// Block-level gradient of one dense layer: dW[o][k] += sum_s cur[o][s] in[k][s],
+// db[o] += sum_s cur[o][s] over the block's kTile samples (columns).
+__device__ void accum_grads(const MLP& a, int L, const float* cur, const float* ain, float* grad) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nin = layer_in(a, L), nout = layer_out(a, L);
+    float* gW = grad + theta_W(a, L);
+    float* gb = grad + theta_b(a, L);
+    for (int p = warp; p < nout * nin; p += kTile / 32) {
+        const int o = p / nin, k = p - o * nin;
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kTile / 32; j++) acc = fmaf(cur[o * kTile + lane + 32 * j], ain[k * kTile + lane + 32 * j], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) atomicAdd(gW + p, acc);
+    }
+    for (int o = warp; o < nout; o += kTile / 32) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kTile / 32; j++) acc += cur[o * kTile + lane + 32 * j];
+        acc = warp_sum(acc);
+        if (lane == 0) atomicAdd(gb + o, acc);
+    }
+}
+
+// Per-sample input gradient of one dense layer for inputs k0 .. k0 + nk - 1:
+// dx[k - k0] = (add ? dx : 0) + sum_o W_L[o][k] cur[o] (W_L[o][k] = wt_L[k][o]),
+// times silu'(pre) of that input when ds is given.
+__device__ void back_input(const MLP& a, int L, const float* cur, float* dx, int k0, int nk, const float* ds,
+                           bool add) {
+    const int s = threadIdx.x, nout = layer_out(a, L), po = pad8(nout);
+    const __nv_bfloat16* W = a.wt + wt_off(a, L);
+    for (int k = k0; k < k0 + nk; k++) {
+        float acc = 0.0f;
+        for (int o0 = 0; o0 < nout; o0 += 8) {
+            float w[8];
+            ld8(W + (int64_t)k * po + o0, w);
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if (o0 + j < nout) acc = fmaf(w[j], cur[(o0 + j) * kTile + s], acc);
+        }
+        float v = add ? dx[(k - k0) * kTile + s] + acc : acc;
+        if (ds) v *= ds[(k - k0) * kTile + s];
+        dx[(k - k0) * kTile + s] = v;
+    }
+}
+
+__host__ __device__ size_t train_block_floats(const MLP& a) {
+    return (size_t)(a.arch ? a.din + 17 * a.hid : kMlpMaxIn + 8 * a.hid) * kTile;
+}
+
+// One training step on a batch (kTile samples per block): forward with the
+// activations and silu' kept in the block's scratch, loss (sample_loss,
+// averaged over the batch), backward, and the weight / bias gradients summed
+// over the block's samples and added to `grad`.  The bf16 rounding of the
+// forward pass is passed through unchanged by the backward pass.
+__global__ void __launch_bounds__(kTile) k_nn_train_step(MLP a, int kind, float wth, int64_t ld, const float* X,
+                                                         const float* Y, const int32_t* perm, int batch, float* grad,
+                                                         float* scratch, float* loss_acc) {
+    const int s = threadIdx.x, lane = s & 31, H = a.hid;
+    float* base = scratch + (size_t)blockIdx.x * train_block_floats(a);
+    const int64_t idx = perm[(int64_t)blockIdx.x * kTile + s];
+    const float inv_b = 1.0f / (float)batch;
+    float outv[16];
+    float l;
+    if (a.arch == 0) {
+        float* u = base;                           // [din][kTile]
+        float* act = u + kMlpMaxIn * kTile;        // [3][H][kTile]
+        float* dsl = act + 3 * H * kTile;          // [3][H][kTile]
+        float* bufA = dsl + 3 * H * kTile;         // [H][kTile]
+        float* bufB = bufA + H * kTile;            // [H][kTile]
+        for (int i = 0; i < a.din; i++) u[i * kTile + s] = X[i * ld + idx];
+        for (int L = 0; L < 3; L++)
+            layer_sample<true>(a, L, (L == 0 ? u : act + (L - 1) * H * kTile) + s, kTile, act + L * H * kTile + s,
+                               kTile, dsl + L * H * kTile + s, kTile);
+        layer_sample<false>(a, 3, act + 2 * H * kTile + s, kTile, outv, 1, nullptr, 0);
+        l = sample_loss(kind, a.dout, wth, outv, Y, ld, idx, inv_b, bufA + s, kTile, nullptr);
+        __syncthreads();
+        float* cur = bufA;
+        float* nxt = bufB;
+        for (int L = 3; L >= 0; L--) {
+            const float* ain = (L == 0) ? u : act + (L - 1) * H * kTile;
+            accum_grads(a, L, cur, ain, grad);
+            if (L > 0) {
+                back_input(a, L, cur, nxt, 0, H, dsl + (L - 1) * H * kTile, false);
+                float* t = cur;
+                cur = nxt;
+                nxt = t;
+            }
+            __syncthreads();
+        }
+    } else {
+        // rows: [u (din)][h3 (H)] contiguous (the output layer's input), h0, h1,
+        // h2, a1, a2, a3, silu' of the 7 hidden pre-activations, three buffers
+        float* u = base;
+        float* h3 = u + a.din * kTile;
+        float* hk = h3 + H * kTile;                // h0, h1, h2
+        float* ak = hk + 3 * H * kTile;            // a1, a2, a3
+        float* dsl = ak + 3 * H * kTile;           // layer 0, then (a_k, c_k) for k = 1..3
+        float* bufA = dsl + 7 * H * kTile;
+        float* bufB = bufA + H * kTile;
+        float* bufC = bufB + H * kTile;
+        auto hp = [&](int k) { return k == 3 ? h3 : hk + k * H * kTile; };
+        for (int i = 0; i < a.din; i++) u[i * kTile + s] = X[i * ld + idx];
+        layer_sample<true>(a, 0, u + s, kTile, hp(0) + s, kTile, dsl + s, kTile);
+        for (int k = 1; k <= 3; k++) {
+            float* ah = ak + (k - 1) * H * kTile;
+            layer_sample<true>(a, 2 * k - 1, hp(k - 1) + s, kTile, ah + s, kTile, dsl + (2 * k - 1) * H * kTile + s,
+                               kTile);
+            layer_sample<true>(a, 2 * k, ah + s, kTile, bufC + s, kTile, dsl + 2 * k * H * kTile + s, kTile);
+            float* hn = hp(k);
+            const float* hpv = hp(k - 1);
+            for (int j = 0; j < H; j++) hn[j * kTile + s] = bf16_round(hpv[j * kTile + s] + bufC[j * kTile + s]);
+        }
+        layer_sample<false>(a, 7, u + s, kTile, outv, 1, nullptr, 0);
+        l = sample_loss(kind, a.dout, wth, outv, Y, ld, idx, inv_b, bufA + s, kTile, nullptr);
+        __syncthreads();
+        accum_grads(a, 7, bufA, u, grad);              // input [u; h3]
+        back_input(a, 7, bufA, bufB, a.din, H, nullptr, false);  // bufB = d h3
+        __syncthreads();
+        for (int k = 3; k >= 1; k--) {
+            // c_k = silu(W_2k a_k + b): d pre = d h_k * silu'
+            for (int j = 0; j < H; j++) bufC[j * kTile + s] = bufB[j * kTile + s] * dsl[(2 * k * H + j) * kTile + s];
+            __syncthreads();
+            accum_grads(a, 2 * k, bufC, ak + (k - 1) * H * kTile, grad);
+            back_input(a, 2 * k, bufC, bufA, 0, H, dsl + (2 * k - 1) * H * kTile, false);  // d pre of a_k
+            __syncthreads();
+            accum_grads(a, 2 * k - 1, bufA, hp(k - 1), grad);
+            back_input(a, 2 * k - 1, bufA, bufB, 0, H, nullptr, true);  // d h_{k-1} = d h_k + W^T d pre
+            __syncthreads();
+        }
+        for (int j = 0; j < H; j++) bufB[j * kTile + s] *= dsl[j * kTile + s];
+        __syncthreads();
+        accum_grads(a, 0, bufB, u, grad);
+        __syncthreads();
     }
     l = warp_sum(l);
     if (lane == 0) atomicAdd(loss_acc, l * inv_b);
-    __syncthreads();
-    float* cur = bufA;
-    float* nxt = bufB;
-    for (int L = 3; L >= 0; L--) {
-        const float* ain = (L == 0) ? u : act + (L - 1) * H * kTile;
-        const int nin = layer_in(a, L), nout = layer_out(a, L);
-        // dW[o][k] = sum_s cur[o][s] ain[k][s]; db[o] = sum_s cur[o][s]
-        float* gW = grad + theta_W(a, L);
-        float* gb = grad + theta_b(a, L);
-        for (int p = warp; p < nout * nin; p += kTile / 32) {
-            const int o = p / nin, k = p - o * nin;
-            float acc = 0.0f;
-#pragma unroll
-            for (int j = 0; j < kTile / 32; j++) acc = fmaf(cur[o * kTile + lane + 32 * j], ain[k * kTile + lane + 32 * j], acc);
-            acc = warp_sum(acc);
-            if (lane == 0) atomicAdd(gW + p, acc);
-        }
-        for (int o = warp; o < nout; o += kTile / 32) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int j = 0; j < kTile / 32; j++) acc += cur[o * kTile + lane + 32 * j];
-            acc = warp_sum(acc);
-            if (lane == 0) atomicAdd(gb + o, acc);
-        }
-        if (L > 0) {
-            // d pre_{L-1}[k] = silu'(pre_{L-1}[k]) sum_o W_L[o][k] cur[o]; W_L[o][k] = wt_L[k][o]
-            const __nv_bfloat16* W = a.wt + wt_off(a, L);
-            const int po = pad8(nout);
-            const float* ds = dsl + (L - 1) * H * kTile;
-            for (int k = 0; k < nin; k++) {
-                float acc = 0.0f;
-                for (int o0 = 0; o0 < nout; o0 += 8) {
-                    float w[8];
-                    ld8(W + (int64_t)k * po + o0, w);
-#pragma unroll
-                    for (int j = 0; j < 8; j++)
-                        if (o0 + j < nout) acc = fmaf(w[j], cur[(o0 + j) * kTile + s], acc);
-                }
-                nxt[k * kTile + s] = acc * ds[k * kTile + s];
-            }
-            float* t = cur;
-            cur = nxt;
-            nxt = t;
-        }
-        __syncthreads();
-    }
 }
 
 // Adam (Kingma & Ba) on the FP32 master; refreshes the BF16 transposed copy
@@ -163,7 +290,7 @@ __global__ void k_nn_adam(MLP a, int64_t np, float* theta, __nv_bfloat16* wt, fl
         v[i] = vi;
         const float th = theta[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
         theta[i] = th;
-        for (int L = 0; L < 4; L++) {
+        for (int L = 0; L < n_layers(a); L++) {
             const int64_t w0 = theta_W(a, L), b0 = theta_b(a, L);
             if (i >= w0 && i < b0) {
                 const int nin = layer_in(a, L);
@@ -174,31 +301,24 @@ __global__ void k_nn_adam(MLP a, int64_t np, float* theta, __nv_bfloat16* wt, fl
     }
 }
 
-// Mean loss and (classifier) number of correct labels at p = 1/2 over X.
-__global__ void __launch_bounds__(kTile) k_nn_eval(MLP a, int kind, int64_t n, const float* X, const float* Y,
-                                                   double* acc) {
+// Mean loss over X and a second statistic: the number of correct labels at
+// p = 1/2 (kind 0) or the summed |theta - theta_hat| (kind 2).
+__global__ void __launch_bounds__(kTile) k_nn_eval(MLP a, int kind, float wth, int64_t n, const float* X,
+                                                   const float* Y, double* acc) {
     extern __shared__ float sm[];
     const int s = threadIdx.x;
-    float* u = sm + s;
-    float* h0 = sm + kMlpMaxIn * kTile + s;
-    float* h1 = h0 + a.hid * kTile;
+    float* col = sm + s;
     for (int64_t base = (int64_t)blockIdx.x * kTile; base < n; base += (int64_t)gridDim.x * kTile) {
         const int64_t m = base + s;
         if (m >= n) continue;
-        for (int i = 0; i < a.din; i++) u[i * kTile] = X[i * n + m];
-        layer_sample<true>(a, 0, u, kTile, h0, kTile, nullptr, 0);
-        layer_sample<true>(a, 1, h0, kTile, h1, kTile, nullptr, 0);
-        layer_sample<true>(a, 2, h1, kTile, h0, kTile, nullptr, 0);
+        for (int i = 0; i < a.din; i++) col[i * kTile] = X[i * n + m];
         float outv[16];
-        layer_sample<false>(a, 3, h0, kTile, outv, 1, nullptr, 0);
-        double l = 0.0, ok = 0.0;
-        if (kind == 0) {
-            const float zz = outv[0], y = Y[m];
-            l = fmaxf(zz, 0.0f) + log1pf(__expf(-fabsf(zz))) - y * zz;
-            ok = ((zz >= 0.0f) == (y >= 0.5f)) ? 1.0 : 0.0;
-        } else {
-            for (int o = 0; o < a.dout; o++) l += fabsf(outv[o] - Y[o * n + m]);
-        }
+        forward_sample(a, col, kTile, outv, 1);
+        float the = 0.0f;
+        const double l = sample_loss(kind, a.dout, wth, outv, Y, n, m, 1.0f, nullptr, 0, &the);
+        double ok = 0.0;
+        if (kind == 0) ok = ((outv[0] >= 0.0f) == (Y[m] >= 0.5f)) ? 1.0 : 0.0;
+        if (kind == 2) ok = the;
         atomicAdd(acc, l);
         atomicAdd(acc + 1, ok);
     }
@@ -240,16 +360,20 @@ cudaError_t nn_infer_launch(const MLP& a, int nc, int64_t n, int64_t ld, const d
 
 extern "C" {
 
-int ptflash_nn_set(ptflash_ctx* c, int which, int hidden, const float* theta, const float* mean, const float* std) {
+int ptflash_nn_set_arch(ptflash_ctx* c, int which, int arch, int hidden, const float* theta, const float* mean,
+                        const float* std) {
     if (!c || which < 0 || which > 1 || !theta || !mean || !std) return PTF_ERR_INVALID_ARG;
     if (!c->have_comp) return PTF_ERR_NOT_READY;
-    if (hidden != 64 && hidden != 128) return PTF_ERR_INVALID_ARG;
+    if (arch == 0 && hidden != 32 && hidden != 64 && hidden != 128) return PTF_ERR_INVALID_ARG;
+    if (arch == 1 && hidden != 32 && hidden != 64) return PTF_ERR_INVALID_ARG;
+    if (arch != 0 && arch != 1) return PTF_ERR_INVALID_ARG;
     const int nc = c->comp.nc, din = nc + 2, dout = which == 0 ? 1 : nc;
     for (int i = 0; i < din; i++)
         if (!(std[i] > 0.0f) || !std::isfinite(mean[i])) return PTF_ERR_INVALID_ARG;
     NNState& N = c->nn[which];
-    const int64_t np = theta_size(din, hidden, dout), nw = wt_size(din, hidden, dout);
-    if (N.ready && (N.din != din || N.hid != hidden || N.dout != dout)) {
+    MLP meta{din, hidden, dout, nullptr, nullptr, nullptr, nullptr, arch};
+    const int64_t np = theta_size(meta), nw = wt_size(meta);
+    if (N.ready && (N.din != din || N.hid != hidden || N.dout != dout || N.arch != arch)) {
         cudaFree(N.theta);
         cudaFree(N.wt);
         cudaFree(N.mean);
@@ -271,10 +395,10 @@ int ptflash_nn_set(ptflash_ctx* c, int which, int hidden, const float* theta, co
     N.din = din;
     N.hid = hidden;
     N.dout = dout;
+    N.arch = arch;
     // BF16 transposed, padded copy built on the host
-    MLP meta{din, hidden, dout, nullptr, nullptr, nullptr, nullptr};
     std::vector<uint16_t> w(nw, 0);
-    for (int L = 0; L < 4; L++) {
+    for (int L = 0; L < n_layers(meta); L++) {
         const int nin = layer_in(meta, L), nout = layer_out(meta, L);
         const float* W = theta + theta_W(meta, L);
         for (int o = 0; o < nout; o++)
@@ -300,20 +424,34 @@ int ptflash_nn_set(ptflash_ctx* c, int which, int hidden, const float* theta, co
     return PTF_OK;
 }
 
+int ptflash_nn_set(ptflash_ctx* c, int which, int hidden, const float* theta, const float* mean, const float* std) {
+    return ptflash_nn_set_arch(c, which, 0, hidden, theta, mean, std);
+}
+
+int ptflash_nn_set_theta_loss(ptflash_ctx* c, int which, float weight) {
+    int rc = nn_check(c, which);
+    if (rc) return rc;
+    if (which != 1 || !(weight >= 0.0f) || !std::isfinite(weight)) return PTF_ERR_INVALID_ARG;
+    c->nn[which].theta_w = weight;
+    return PTF_OK;
+}
+
 int ptflash_nn_get(ptflash_ctx* c, int which, float* theta) {
     int rc = nn_check(c, which);
     if (rc) return rc;
     if (!theta) return PTF_ERR_INVALID_ARG;
     const NNState& N = c->nn[which];
     NN_CUDA(cudaDeviceSynchronize());
-    NN_CUDA(cudaMemcpy(theta, N.theta, theta_size(N.din, N.hid, N.dout) * 4, cudaMemcpyDeviceToHost));
+    NN_CUDA(cudaMemcpy(theta, N.theta, theta_size(N.view()) * 4, cudaMemcpyDeviceToHost));
     return PTF_OK;
 }
 
-int64_t ptflash_nn_param_count(int din, int hidden, int dout) {
-    if (din < 1 || din > kMlpMaxIn || hidden < 1 || dout < 1 || dout > 16) return 0;
-    return theta_size(din, hidden, dout);
+int64_t ptflash_nn_param_count_arch(int arch, int din, int hidden, int dout) {
+    if (din < 1 || din > kMlpMaxIn || hidden < 1 || dout < 1 || dout > 16 || (arch != 0 && arch != 1)) return 0;
+    return theta_size(MLP{din, hidden, dout, nullptr, nullptr, nullptr, nullptr, arch});
 }
+
+int64_t ptflash_nn_param_count(int din, int hidden, int dout) { return ptflash_nn_param_count_arch(0, din, hidden, dout); }
 
 int ptflash_nn_features(ptflash_ctx* c, int which, int64_t n, const double* P, const double* T, const double* z,
                         float* X, void* stream) {
@@ -358,7 +496,8 @@ int ptflash_nn_train_steps(ptflash_ctx* c, int which, int64_t n, const float* X,
         }
         c->train_scratch_bytes = need;
     }
-    const int64_t np = theta_size(N.din, N.hid, N.dout);
+    const int64_t np = theta_size(a);
+    const int kind = which == 0 ? 0 : (N.theta_w > 0.0f ? 2 : 1);
     float* dummy_loss = nullptr;
     if (!loss) {
         NN_CUDA(cudaMalloc(&dummy_loss, sizeof(float)));
@@ -366,7 +505,7 @@ int ptflash_nn_train_steps(ptflash_ctx* c, int which, int64_t n, const float* X,
     for (int64_t k = 0; k < steps; k++) {
         float* lk = loss ? loss + k : dummy_loss;
         if (!loss) NN_CUDA(cudaMemsetAsync(dummy_loss, 0, sizeof(float), s));
-        k_nn_train_step<<<batch / kTile, kTile, 0, s>>>(a, which, n, X, Y, perm + k * batch, batch, N.grad,
+        k_nn_train_step<<<batch / kTile, kTile, 0, s>>>(a, kind, N.theta_w, n, X, Y, perm + k * batch, batch, N.grad,
                                                         c->train_scratch, lk);
         N.t++;
         const float bc1 = 1.0f - std::pow(beta1, (float)N.t), bc2 = 1.0f - std::pow(beta2, (float)N.t);
@@ -388,6 +527,7 @@ int ptflash_nn_eval(ptflash_ctx* c, int which, int64_t n, const float* X, const 
     if (rc) return rc;
     if (n < 1 || !X || !Y || !loss) return PTF_ERR_INVALID_ARG;
     const MLP a = c->nn[which].view();
+    const int kind = which == 0 ? 0 : (c->nn[which].theta_w > 0.0f ? 2 : 1);
     cudaStream_t s = (cudaStream_t)stream;
     double* d = nullptr;
     NN_CUDA(cudaMalloc(&d, 2 * sizeof(double)));
@@ -400,7 +540,7 @@ int ptflash_nn_eval(ptflash_ctx* c, int which, int64_t n, const float* X, const 
     if (e == cudaSuccess) {
         const int64_t tiles = (n + kTile - 1) / kTile;
         const int grid = (int)(tiles < (int64_t)c->sm_count * 8 ? tiles : (int64_t)c->sm_count * 8);
-        k_nn_eval<<<grid, kTile, infer_smem(a), s>>>(a, which, n, X, Y, d);
+        k_nn_eval<<<grid, kTile, infer_smem(a), s>>>(a, kind, c->nn[which].theta_w, n, X, Y, d);
         e = cudaGetLastError();
     }
     double h[2] = {0, 0};

@@ -19,6 +19,12 @@ from . import ptflash, workloads as wl
 
 CLASSIFIER, INITIALIZER = 0, 1
 HIDDEN = {CLASSIFIER: 64, INITIALIZER: 128}
+# (arch, hidden) per network.  DEFAULT_NETS: 3-hidden-layer networks of 64 and
+# 128 units.  PAPER_NETS: the paper's classifier (3 x 32, Sec. 4.1.1) and
+# initializer (a hidden layer, 3 residual blocks, wide output; 64 units,
+# Sec. 4.2.1).
+DEFAULT_NETS = {CLASSIFIER: (0, 64), INITIALIZER: (0, 128)}
+PAPER_NETS = {CLASSIFIER: (0, 32), INITIALIZER: (1, 64)}
 
 
 @dataclass
@@ -30,6 +36,10 @@ class TrainConfig:
     half_cycle_epochs: int = 2      # triangular CLR: steps per half cycle = this x steps per epoch
     patience: int = 6               # early stopping on the validation loss
     seed: int = 7
+    nets: dict = field(default_factory=lambda: dict(DEFAULT_NETS))
+    stage2_epochs: int = 0          # initializer second stage: + |theta - theta_hat| (Sec. 4.2.2)
+    stage2_lr: float = 1e-5
+    stage2_weight: float = 1.0
 
 
 @dataclass
@@ -38,6 +48,7 @@ class TrainLog:
     best_epoch: int = -1
     test_loss: float = float("nan")
     test_acc: float = float("nan")
+    test_mae_lnK: float = float("nan")
 
 
 def clr(step: np.ndarray, half: int, lo: float, hi: float) -> np.ndarray:
@@ -72,10 +83,16 @@ def split_indices(n: int, seed: int):
     return p[:a], p[a:b], p[b:]
 
 
+def dout_of(fl, which):
+    return 1 if which == CLASSIFIER else fl.nc
+
+
 def train_network(fl: ptflash.Flash, which: int, X, Y, idx_train, idx_val, idx_test, cfg: TrainConfig,
-                  log_fn=None) -> TrainLog:
+                  log_fn=None, epochs=None, constant_lr=False) -> TrainLog:
     """Train one network in place (its parameters and scaler must be set).
-    X [din, n], Y [dout, n] device float32 tensors over the whole dataset."""
+    X [din, n], Y [rows, n] device float32 tensors over the whole dataset
+    (rows: the loss's target rows).  CLR between lr_min and lr_max, or the
+    constant stage2_lr with constant_lr."""
     import torch
     dev = X.device
     Xtr, Ytr = X[:, idx_train].contiguous(), Y[:, idx_train].contiguous()
@@ -84,14 +101,16 @@ def train_network(fl: ptflash.Flash, which: int, X, Y, idx_train, idx_val, idx_t
     ntr = Xtr.shape[1]
     steps = ntr // cfg.batch
     half = cfg.half_cycle_epochs * steps
-    nparam = ptflash.load().ptflash_nn_param_count(X.shape[0], HIDDEN[which], Y.shape[0])
+    arch, hid = cfg.nets[which]
+    nparam = ptflash.load().ptflash_nn_param_count_arch(arch, X.shape[0], hid, dout_of(fl, which))
     best, best_val, bad = None, float("inf"), 0
     log = TrainLog()
     loss_dev = torch.zeros(steps, dtype=torch.float32, device=dev)
-    for ep in range(cfg.epochs):
+    for ep in range(cfg.epochs if epochs is None else epochs):
         t0 = time.time()
         perm = torch.tensor(wl.epoch_permutation(ntr, cfg.seed, ep)[: steps * cfg.batch], device=dev)
-        lr = clr(np.arange(ep * steps, (ep + 1) * steps), half, cfg.lr_min, cfg.lr_max)
+        lr = (np.full(steps, cfg.stage2_lr, np.float32) if constant_lr else
+              clr(np.arange(ep * steps, (ep + 1) * steps), half, cfg.lr_min, cfg.lr_max))
         loss_dev.zero_()
         fl.ptflash_nn_train_steps(which, Xtr, Ytr, perm, steps, cfg.batch, lr, loss=loss_dev)
         tl = float(loss_dev.mean().item())
@@ -107,43 +126,62 @@ def train_network(fl: ptflash.Flash, which: int, X, Y, idx_train, idx_val, idx_t
             if bad >= cfg.patience:
                 break
     mean, std = fl._nn_scaler[which]
-    fl.ptflash_nn_set(which, HIDDEN[which], best, mean, std)
+    if best is not None:
+        fl.ptflash_nn_set(which, hid, best, mean, std, arch=arch)
     log.test_loss, log.test_acc = fl.ptflash_nn_eval(which, Xte, Yte)
     return log
 
 
 def train_both(fl: ptflash.Flash, cond: wl.Conditions, cfg: TrainConfig = TrainConfig(), log_fn=None):
     """Generate plain-method labels for `cond`, then train the classifier on
-    all samples and the initializer on the two-phase ones (Sec. 4)."""
+    all samples and the initializer on the two-phase ones (Sec. 4); with
+    cfg.stage2_epochs, a second initializer stage adds the |theta -
+    theta_hat| term at the constant rate stage2_lr (Sec. 4.2.2)."""
     import torch
     nc = fl.nc
     P, T, z, out = make_dataset(fl, cond)
     nphase = out.nphase
     mean, std = feature_stats(cond.P, cond.T, cond.z)
     fl._nn_scaler = {}
+    fl._nn_arch = {}
     logs = {}
     for which in (CLASSIFIER, INITIALIZER):
-        dout = 1 if which == CLASSIFIER else nc
-        theta = wl.mlp_init(nc + 2, HIDDEN[which], dout, cfg.seed + which)
-        fl.ptflash_nn_set(which, HIDDEN[which], theta, mean, std)
+        arch, hid = cfg.nets[which]
+        theta = init_params(nc + 2, hid, dout_of(fl, which), cfg.seed + which, arch)
+        fl.ptflash_nn_set(which, hid, theta, mean, std, arch=arch)
         fl._nn_scaler[which] = (mean, std)
+        fl._nn_arch[which] = (arch, hid)
+    fl.ptflash_nn_set_theta_loss(INITIALIZER, 0.0)
     X = torch.empty(nc + 2, cond.n, dtype=torch.float32, device=P.device)
     fl.ptflash_nn_features(CLASSIFIER, P, T, z, X)
     # classifier on every sample: y = 1 stable (single phase)
     Yc = (nphase == 1).to(torch.float32)[None, :].contiguous()
     tr, va, te = split_indices(cond.n, cfg.seed)
-    logs[CLASSIFIER] = train_network(fl, CLASSIFIER, X, Yc, torch.tensor(tr, device=P.device),
-                                     torch.tensor(va, device=P.device), torch.tensor(te, device=P.device), cfg,
-                                     log_fn)
+    dev = P.device
+    logs[CLASSIFIER] = train_network(fl, CLASSIFIER, X, Yc, torch.tensor(tr, device=dev),
+                                     torch.tensor(va, device=dev), torch.tensor(te, device=dev), cfg, log_fn)
     # initializer on the two-phase samples: ln K targets
     two = torch.nonzero(nphase == 2).flatten()
     X2 = X[:, two].contiguous()
     Y2 = torch.log(out.K[:, two]).to(torch.float32).contiguous()
     tr, va, te = split_indices(int(two.shape[0]), cfg.seed + 1)
-    logs[INITIALIZER] = train_network(fl, INITIALIZER, X2, Y2, torch.tensor(tr, device=P.device),
-                                      torch.tensor(va, device=P.device), torch.tensor(te, device=P.device), cfg,
-                                      log_fn)
+    ti, vi, tei = (torch.tensor(a, device=dev) for a in (tr, va, te))
+    logs[INITIALIZER] = train_network(fl, INITIALIZER, X2, Y2, ti, vi, tei, cfg, log_fn)
+    if cfg.stage2_epochs > 0:
+        # second stage: targets [ln K; theta; z], loss mae(ln K) + w mae(theta)
+        Y3 = torch.cat([Y2, out.beta[two][None, :].to(torch.float32), z[:, two].to(torch.float32)], 0).contiguous()
+        fl.ptflash_nn_set_theta_loss(INITIALIZER, cfg.stage2_weight)
+        logs["stage2"] = train_network(fl, INITIALIZER, X2, Y3, ti, vi, tei, cfg, log_fn, epochs=cfg.stage2_epochs,
+                                       constant_lr=True)
+        # first-stage loss on the test set, for comparison
+        fl.ptflash_nn_set_theta_loss(INITIALIZER, 0.0)
+        logs["stage2"].test_mae_lnK = fl.ptflash_nn_eval(INITIALIZER, X2[:, tei].contiguous(), Y2[:, tei].contiguous())[0]
     return logs
+
+
+def init_params(din, hid, dout, seed, arch=0):
+    """Seeded Glorot-uniform weights and zero biases for either architecture."""
+    return wl.mlp_init(din, hid, dout, seed, arch)
 
 
 def save(fl: ptflash.Flash, path: str, meta: dict | None = None):
@@ -151,13 +189,15 @@ def save(fl: ptflash.Flash, path: str, meta: dict | None = None):
     parameters, then both scalers) and a JSON header beside it."""
     nc = fl.nc
     parts, header = [], {"nc": nc, "nets": []}
+    arch_of = getattr(fl, "_nn_arch", {w: DEFAULT_NETS[w] for w in (CLASSIFIER, INITIALIZER)})
     for which in (CLASSIFIER, INITIALIZER):
-        dout = 1 if which == CLASSIFIER else nc
-        cnt = ptflash.load().ptflash_nn_param_count(nc + 2, HIDDEN[which], dout)
+        arch, hid = arch_of[which]
+        dout = dout_of(fl, which)
+        cnt = ptflash.load().ptflash_nn_param_count_arch(arch, nc + 2, hid, dout)
         th = fl.ptflash_nn_get(which, cnt)
         mean, std = fl._nn_scaler[which]
         parts += [th, mean, std]
-        header["nets"].append({"which": which, "hidden": HIDDEN[which], "dout": dout, "count": int(cnt)})
+        header["nets"].append({"which": which, "arch": arch, "hidden": hid, "dout": dout, "count": int(cnt)})
     header.update(meta or {})
     np.concatenate(parts).astype(np.float32).tofile(path + ".bin")
     with open(path + ".json", "w") as f:
@@ -172,13 +212,16 @@ def load_checkpoint(fl: ptflash.Flash, path: str):
     flat = np.fromfile(path + ".bin", dtype=np.float32)
     k, d = 0, fl.nc + 2
     fl._nn_scaler = {}
+    fl._nn_arch = {}
     for net in header["nets"]:
         th = flat[k:k + net["count"]]
         k += net["count"]
         mean, std = flat[k:k + d], flat[k + d:k + 2 * d]
         k += 2 * d
-        fl.ptflash_nn_set(net["which"], net["hidden"], th, mean, std)
+        arch = net.get("arch", 0)
+        fl.ptflash_nn_set(net["which"], net["hidden"], th, mean, std, arch=arch)
         fl._nn_scaler[net["which"]] = (mean, std)
+        fl._nn_arch[net["which"]] = (arch, net["hidden"])
     return header
 
 

@@ -62,6 +62,10 @@ def load(path: str = LIB_PATH):
     lib.ptflash_last_stage_ms.argtypes = [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     _F = ctypes.POINTER(ctypes.c_float)
     lib.ptflash_nn_set.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _F, _F, _F]
+    lib.ptflash_nn_set_arch.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _F, _F, _F]
+    lib.ptflash_nn_set_theta_loss.argtypes = [_VP, ctypes.c_int, ctypes.c_float]
+    lib.ptflash_nn_param_count_arch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.ptflash_nn_param_count_arch.restype = ctypes.c_int64
     lib.ptflash_nn_get.argtypes = [_VP, ctypes.c_int, _F]
     lib.ptflash_nn_param_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.ptflash_nn_param_count.restype = ctypes.c_int64
@@ -72,7 +76,7 @@ def load(path: str = LIB_PATH):
     lib.ptflash_nn_eval.argtypes = [_VP, ctypes.c_int, _I64, _VP, _VP, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double), _VP]
     for f in ("ptflash_nn_set", "ptflash_nn_get", "ptflash_nn_features", "ptflash_nn_infer", "ptflash_nn_train_steps",
-              "ptflash_nn_eval"):
+              "ptflash_nn_eval", "ptflash_nn_set_arch", "ptflash_nn_set_theta_loss"):
         getattr(lib, f).restype = ctypes.c_int
     lib.ptflash_flash_adjoint.argtypes = [_VP, _I64] + [_VP] * 15
     lib.ptflash_flash_adjoint.restype = ctypes.c_int
@@ -237,10 +241,13 @@ class Flash:
         return dict(zip(self.STAGES, list(ms)))
 
     # ---- learned form (Sec. 4): which = 0 classifier, 1 initializer ----
-    def ptflash_nn_set(self, which: int, hidden: int, theta, mean, std):
+    def ptflash_nn_set(self, which: int, hidden: int, theta, mean, std, arch: int = 0):
         F = ctypes.POINTER(ctypes.c_float)
         arrs = [np.ascontiguousarray(a, np.float32) for a in (theta, mean, std)]
-        _check(load().ptflash_nn_set(self._h, which, hidden, *[a.ctypes.data_as(F) for a in arrs]))
+        _check(load().ptflash_nn_set_arch(self._h, which, arch, hidden, *[a.ctypes.data_as(F) for a in arrs]))
+
+    def ptflash_nn_set_theta_loss(self, which: int, weight: float):
+        _check(load().ptflash_nn_set_theta_loss(self._h, which, float(weight)))
 
     def ptflash_nn_get(self, which: int, count: int):
         out = np.zeros(count, np.float32)

@@ -1,0 +1,65 @@
+"""Train the paper's own networks (Sec. 4) on the GPU with the library's
+kernels: the classifier of 3 x 32 SiLU units (Sec. 4.1.1) and the
+initializer with a hidden layer, three residual blocks and a wide output of
+64 units (Sec. 4.2.1), on plain-method flashes of the 9-component case study
+(Sec. 2.3: Table 1 components, four fluid types, P 5-25 MPa, T 200-600 K).
+The initializer's second stage adds |theta - theta_hat| at the constant rate
+1e-5 (Sec. 4.2.2).  Writes the checkpoint used by the learned form of that
+case.
+
+    python -m paper_2205_03090_gb300.train_paper_nn [--n 1000000] [--epochs 30] [--stage2-epochs 4] [--out PATH]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_OUT = os.path.join(HERE, "weights", "c9_paper")
+TRAIN_SEED = 201  # inputs drawn apart from the benchmark's
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--stage2-epochs", type=int, default=4)
+    ap.add_argument("--out", default=DEFAULT_OUT)
+    args = ap.parse_args(argv)
+    from . import build, nn, ptflash, workloads as wl
+    build.build()
+    t0 = time.time()
+    comp, cond, ft = wl.paper_case("c9", args.n, TRAIN_SEED)
+    t_gen = time.time() - t0
+    fl = ptflash.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=args.n)
+    cfg = nn.TrainConfig(epochs=args.epochs, nets=dict(nn.PAPER_NETS), stage2_epochs=args.stage2_epochs)
+    t0 = time.time()
+    logs = nn.train_both(fl, cond, cfg, log_fn=print)
+    dt = time.time() - t0
+    os.makedirs(os.path.dirname(args.out), exist_ok=True)
+    nc = comp.nc
+    meta = {"workload": "paper case study, 9 components (Table 1), four fluid types (Tables 2-3), P 5-25 MPa, "
+                        "T 200-600 K",
+            "train_samples": args.n, "train_seed": TRAIN_SEED, "seconds": dt, "input_seconds": t_gen,
+            "classifier": {"arch": "3 x 32 SiLU", "best_epoch": logs[0].best_epoch, "test_bce": logs[0].test_loss,
+                           "test_accuracy": logs[0].test_acc},
+            "initializer": {"arch": "1 + 3 residual blocks x 2, 64 SiLU, wide output",
+                            "best_epoch": logs[1].best_epoch, "test_mae_lnK_sum": logs[1].test_loss,
+                            "test_mae_lnK_per_component": logs[1].test_loss / nc}}
+    if "stage2" in logs:
+        s2 = logs["stage2"]
+        meta["initializer"]["stage2"] = {"epochs_run": len(s2.epochs), "best_epoch": s2.best_epoch,
+                                         "test_loss": s2.test_loss, "test_mae_theta": s2.test_acc,
+                                         "test_mae_lnK_sum": s2.test_mae_lnK,
+                                         "test_mae_lnK_per_component": s2.test_mae_lnK / nc}
+    nn.save(fl, args.out, meta)
+    print(json.dumps(meta))
+    fl.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

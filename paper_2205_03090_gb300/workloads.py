@@ -243,13 +243,16 @@ def paper_case(case: str, n: int, seed: int = 0):
     return comp, Conditions(np.concatenate(Ps), np.concatenate(Ts), np.ascontiguousarray(z.T)), np.concatenate(ft)
 
 
-def mlp_init(din: int, hidden: int, dout: int, seed: int) -> np.ndarray:
+def mlp_init(din: int, hidden: int, dout: int, seed: int, arch: int = 0) -> np.ndarray:
     """Initial network parameters drawn from seeded Glorot-uniform
-    distributions (weights) with zero biases, in the flat order W1, b1, W2,
-    b2, W3, b3, W4, b4 (each W row-major [out, in])."""
+    distributions (weights) with zero biases, in the flat order W_0, b_0,
+    W_1, b_1, ... (each W row-major [out, in]).  arch 0: three hidden layers;
+    arch 1: a hidden layer, six residual-block layers, output on [u; h]."""
     g = np.random.Generator(np.random.PCG64(seed))
     parts = []
-    for o, i in [(hidden, din), (hidden, hidden), (hidden, hidden), (dout, hidden)]:
+    shapes = ([(hidden, din)] + [(hidden, hidden)] * 6 + [(dout, din + hidden)] if arch == 1 else
+              [(hidden, din), (hidden, hidden), (hidden, hidden), (dout, hidden)])
+    for o, i in shapes:
         lim = np.sqrt(6.0 / (i + o))
         parts.append(g.uniform(-lim, lim, o * i))
         parts.append(np.zeros(o))
