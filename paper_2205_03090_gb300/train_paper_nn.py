@@ -7,7 +7,12 @@ The initializer's second stage adds |theta - theta_hat| at the constant rate
 1e-5 (Sec. 4.2.2).  Writes the checkpoint used by the learned form of that
 case.
 
-    python -m paper_2205_03090_gb300.train_paper_nn [--n 1000000] [--epochs 30] [--stage2-epochs 4] [--out PATH]
+    python -m paper_2205_03090_gb300.train_paper_nn [--n 1000000] [--epochs 30] [--stage2-epochs 4]
+        [--patience 6] [--out PATH]
+
+The committed checkpoint was trained with --n 2700000 --epochs 60
+--stage2-epochs 10 --patience 8: about 1e6 of the 2.7e6 mixtures are two-phase,
+the size of the paper's initializer set (Sec. 4.2.2).
 """
 from __future__ import annotations
 
@@ -27,6 +32,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--stage2-epochs", type=int, default=4)
+    ap.add_argument("--patience", type=int, default=6)
     ap.add_argument("--out", default=DEFAULT_OUT)
     args = ap.parse_args(argv)
     from . import build, nn, ptflash, workloads as wl
@@ -35,7 +41,8 @@ def main(argv=None):
     comp, cond, ft = wl.paper_case("c9", args.n, TRAIN_SEED)
     t_gen = time.time() - t0
     fl = ptflash.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=args.n)
-    cfg = nn.TrainConfig(epochs=args.epochs, nets=dict(nn.PAPER_NETS), stage2_epochs=args.stage2_epochs)
+    cfg = nn.TrainConfig(epochs=args.epochs, nets=dict(nn.PAPER_NETS), stage2_epochs=args.stage2_epochs,
+                         patience=args.patience)
     t0 = time.time()
     logs = nn.train_both(fl, cond, cfg, log_fn=print)
     dt = time.time() - t0
