@@ -46,6 +46,30 @@ LEARNED_DESC = ("10 SRK pseudo-components drawn as above, 1e7 mixtures, T~U(250,
                 "p_l=0.02, p_r=0.98")
 
 
+def rank_conditions(w: dict, n: int, rank: int):
+    """This rank's shard of the workload: the same distribution, its own seed
+    (weak scaling: every rank flashes n mixtures of its own)."""
+    from paper_2205_03090_gb300 import workloads as wl
+    return wl.conditions(w["nc"], n, w["cond_seed"] + 1000 * rank, w["T_range"], w["P_range"], w["alpha"])
+
+
+def job_ms(ms: float, dist, device) -> float:
+    """The job's time per step: the maximum over ranks (every rank's value
+    when there is one rank)."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_per_rank: int, ws: int, frac: float, ms: float) -> float:
+    """Whole-job throughput: oracle-matching flashes of all ranks per second
+    (NaN without an oracle-matching fraction: a diagnostic run)."""
+    return ws * n_per_rank * frac / (ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -408,7 +432,7 @@ def ours_arm(args, ws, rank, local):
     w = dict(wl.WORKLOADS[WORKLOAD])
     comp = wl.pseudo_components(w["nc"], w["comp_seed"])
     n_mix = args.n or w["n"]
-    cond = wl.conditions(w["nc"], n_mix, w["cond_seed"] + 1000 * rank, w["T_range"], w["P_range"], w["alpha"])
+    cond = rank_conditions(w, n_mix, rank)
     n, nc = cond.n, comp.nc
     fl = ptflash.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=n)
     P = torch.tensor(cond.P, device=dev)
@@ -447,11 +471,7 @@ def ours_arm(args, ws, rank, local):
         dist.barrier()
     clk = clocks.stop()
     fl.ptflash_set_profiling(False)
-    ms = float(np.mean(step_ms))
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_ms(float(np.mean(step_ms)), dist, dev)
     counts = fl.ptflash_last_counts()
     g = {k: getattr(out, k).cpu().numpy() for k in ("nphase", "beta", "x", "y", "status")}
 
@@ -514,7 +534,7 @@ def ours_arm(args, ws, rank, local):
         achieved = work / (mean_stage[dom] / 1e3) / 1e12
     else:
         work, achieved = None, None
-    value = ws * n * frac / (ms / 1e3)
+    value = job_value(n, ws, frac, ms)
     line = {
         "metric": METRIC, "value": value, "unit": "flashes/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
