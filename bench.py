@@ -46,6 +46,13 @@ LEARNED_DESC = ("10 SRK pseudo-components drawn as above, 1e7 mixtures, T~U(250,
                 "p_l=0.02, p_r=0.98")
 
 
+# DRAM bytes per unit of work of a kernel, from one ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum (profiles/ncu_stab_ss_nc8_3e5.md:
+# k_stab_ss on 3e5 mixtures, 381,526 trial items, 143.4 MB); the bench scales
+# it by this run's units.  Only valid for the kernel as captured.
+TRAFFIC_PER_UNIT = {"stab_ss": (143.384e6 / 381526, "trial items", lambda q: 2 * q["stab"])}
+
+
 def rank_conditions(w: dict, n: int, rank: int):
     """This rank's shard of the workload: the same distribution, its own seed
     (weak scaling: every rank flashes n mixtures of its own)."""
@@ -534,6 +541,12 @@ def ours_arm(args, ws, rank, local):
         achieved = work / (mean_stage[dom] / 1e3) / 1e12
     else:
         work, achieved = None, None
+    traffic, traffic_src = None, None
+    if dom in TRAFFIC_PER_UNIT:
+        per, unit, count = TRAFFIC_PER_UNIT[dom]
+        traffic = per * count(counts)
+        traffic_src = (f"ncu dram bytes of k_{dom} on a 3e5-mixture case, {per:.0f} B per {unit[:-1]}, "
+                       f"x {count(counts)} {unit} of this launch")
     value = job_value(n, ws, frac, ms)
     line = {
         "metric": METRIC, "value": value, "unit": "flashes/s", "n_gpus": ws, "steps": args.steps,
@@ -543,7 +556,8 @@ def ours_arm(args, ws, rank, local):
                    "l2": "flushed between steps (512 MB write); inputs resident in HBM"},
         "oracle_match": {"frac": frac, "sample": sample, "tol": TOL},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_source": traffic_src,
                      "peak_source": f"152 SMs x 2 FP64 FMA/clk x 2 flop x {sm_mhz:.0f} MHz (sampled median)",
                      "work_per_launch_flop": work},
         "stage_ms": mean_stage,
