@@ -300,13 +300,15 @@ int ptflash_nn_eval(ptflash_ctx* ctx, int which, int64_t n, const float* X, cons
                     double* accuracy, void* stream);
 
 /*
- * Self-check of the library's own table-driven logarithm (used on every hot
- * path) against the CUDA math library's log, on the current device:
- * 2n inputs (log-uniform over [1e-300, 1e300] and uniform over [0.5, 2]);
- * *max_ulp_log receives the largest error in units of the last place.
- * Allocates a few bytes of device memory and synchronises the device.
+ * Self-check of the library's own table-driven logarithm and exponential
+ * (used on every hot path) against the CUDA math library, on the current
+ * device.  log: 2n inputs (log-uniform over [1e-300, 1e300] and uniform over
+ * [0.5, 2]); exp: 2n inputs (uniform over [-700, 700] and over [-40, 10]).
+ * *max_ulp_log and *max_ulp_exp receive the largest errors in units of the
+ * last place of the library's result.  Allocates a few bytes of device
+ * memory and synchronises the device.
  */
-int ptflash_check_math(int64_t n, double* max_ulp_log);
+int ptflash_check_math(int64_t n, double* max_ulp_log, double* max_ulp_exp);
 
 /* Human-readable name of an error code. */
 const char* ptflash_strerror(int code);

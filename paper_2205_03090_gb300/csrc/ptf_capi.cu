@@ -50,41 +50,47 @@ static cudaError_t dispatch(ptflash_ctx* c, const WS& ws, const IO& io, int mode
 }
 
 // Self-check of the library's own elementary functions against the CUDA math
-// library: n inputs spread log-uniformly over [1e-300, 1e300] plus n inputs
-// in [0.5, 2]; the largest error in units of the last place of the library
-// result is folded into *err (positive doubles order like their bit patterns).
-__global__ void k_check_log(int64_t n, unsigned long long* err) {
+// library.  log: n inputs spread log-uniformly over [1e-300, 1e300] plus n
+// inputs in [0.5, 2].  exp: n inputs uniform over [-700, 700] plus n in
+// [-40, 10].  The largest error in units of the last place of the library
+// result is folded into err[0] (log) and err[1] (exp) (positive doubles
+// order like their bit patterns).
+__device__ __forceinline__ double ulp_of(double ref) {
+    if (ref == 0.0) return 4.9e-324;
+    int ex;
+    frexp(ref, &ex);
+    return ldexp(1.0, ex - 53);
+}
+
+__global__ void k_check_math(int64_t n, unsigned long long* err) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 2 * n; k += (int64_t)gridDim.x * blockDim.x) {
         const double u = (double)(k % n) / (double)n;
         const double x = (k < n) ? exp2(-996.0 + 1992.0 * u) * (1.0 + 0.61803398874989 * u) : 0.5 + 1.5 * u;
         const double ref = log(x), got = log_fast(x);
-        double ulp = 4.9e-324;
-        if (ref != 0.0) {
-            int ex;
-            frexp(ref, &ex);
-            ulp = ldexp(1.0, ex - 53);
-        }
-        const double e = fabs(got - ref) / ulp;
-        atomicMax(err, (unsigned long long)__double_as_longlong(e));
+        atomicMax(err, (unsigned long long)__double_as_longlong(fabs(got - ref) / ulp_of(ref)));
+        const double y = (k < n) ? -700.0 + 1400.0 * u : -40.0 + 50.0 * u;
+        const double re = exp(y), ge = exp_fast(y);
+        atomicMax(err + 1, (unsigned long long)__double_as_longlong(fabs(ge - re) / ulp_of(re)));
     }
 }
 
 extern "C" {
 
-int ptflash_check_math(int64_t n, double* max_ulp_log) {
-    if (n < 1 || n > (int64_t)1 << 28 || !max_ulp_log) return PTF_ERR_INVALID_ARG;
+int ptflash_check_math(int64_t n, double* max_ulp_log, double* max_ulp_exp) {
+    if (n < 1 || n > (int64_t)1 << 28 || !max_ulp_log || !max_ulp_exp) return PTF_ERR_INVALID_ARG;
     unsigned long long* d = nullptr;
-    PTF_CUDA(cudaMalloc(&d, sizeof(unsigned long long)));
-    cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
+    PTF_CUDA(cudaMalloc(&d, 2 * sizeof(unsigned long long)));
+    cudaError_t e = cudaMemset(d, 0, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) {
-        k_check_log<<<1024, 256>>>(n, d);
+        k_check_math<<<1024, 256>>>(n, d);
         e = cudaGetLastError();
     }
-    unsigned long long h = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    unsigned long long h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
     cudaFree(d);
     if (e != cudaSuccess) return cuda_fail(e);
-    *max_ulp_log = __builtin_bit_cast(double, h);
+    *max_ulp_log = __builtin_bit_cast(double, h[0]);
+    *max_ulp_exp = __builtin_bit_cast(double, h[1]);
     return PTF_OK;
 }
 

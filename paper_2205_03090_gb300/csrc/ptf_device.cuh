@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "ptf_logtab.cuh"
+#include "ptf_exptab.cuh"
 
 namespace ptf {
 
@@ -95,6 +96,33 @@ __device__ __forceinline__ double log_fast(double x) {
     const double l1p = fma(t, r * r, r);
     const double ed = __longlong_as_double(0x4338000000000000LL + e) - 6755399441055744.0;  // (double)e
     return fma(ed, 0.6931471805599453, lnF + l1p);
+}
+
+// ---------------------------------------------------------------------------
+// Exponential for |x| < 708 by the table-driven method of P. T. P. Tang (ACM
+// TOMS 15 (1989) 144): n = rint(64 x / ln 2) = 64 m + j, r = x - n ln2/64
+// (two-part constant, |r| <= ln2/128), e^x = 2^m 2^(j/64) (1 + p(r)) with
+// p(r) = e^r - 1 by its Taylor polynomial to r^6 (truncation below 3e-20).
+// About 12 FP64 operations; outside the range (overflow, underflow, NaN) the
+// library exp.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double exp_fast(double x) {
+    if (!(fabs(x) < 708.0)) return exp(x);
+    const double shifter = 6755399441055744.0;  // 1.5 * 2^52: rint into the low bits
+    const double t = fma(x, kExpInvL, shifter);
+    const int n = (int)__double2loint(t);
+    const double nf = t - shifter;
+    double r = fma(-nf, kExpL1, x);
+    r = fma(-nf, kExpL2, r);
+    double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+    q = fma(q, r, 1.0 / 24.0);
+    q = fma(q, r, 1.0 / 6.0);
+    q = fma(q, r, 0.5);
+    const double p = fma(q, r * r, r);
+    const double T = __ldg(&kExpTab[n & 63]);
+    const double v = fma(T, p, T);
+    // times 2^m, m = n >> 6 (floor): add m to the exponent field
+    return __longlong_as_double(__double_as_longlong(v) + ((long long)(n >> 6) << 52));
 }
 
 // Per-mixture EOS constants: sqrt(A_i) and B_i (reduced, R cancels).

@@ -228,7 +228,7 @@ struct PrecheckSS {
         double K[NC], t[NC], x[NC], y[NC];
         Phase<NC> pl, pv;
 #pragma unroll
-        for (int i = 0; i < NC; i++) K[i] = exp(lnK[i]);
+        for (int i = 0; i < NC; i++) K[i] = exp_fast(lnK[i]);
         if (!rachford_rice<NC>(z, K, th, t) || !(th > 0.0 && th < 1.0)) {
             io.status[m] = ST_STAB_RUN;
             return 1;
@@ -298,7 +298,7 @@ __device__ __forceinline__ bool stab_eval(const Comp<NC>& cp, const Mix<NC>& mx,
     Wt = 0.0;
 #pragma unroll
     for (int i = 0; i < NC; i++) {
-        W[i] = exp(lnW[i]);
+        W[i] = exp_fast(lnW[i]);
         Wt += W[i];
     }
     double inv = 1.0 / Wt;
@@ -539,7 +539,7 @@ struct StabTR {
             }
             cur = nxt;
 #pragma unroll
-            for (int i = 0; i < NC; i++) beta[i] = 2.0 * exp(0.5 * cur.lnW[i]);
+            for (int i = 0; i < NC; i++) beta[i] = 2.0 * exp_fast(0.5 * cur.lnW[i]);
             phase = 1;
         } else {
             const bool trusted = fabs(pred) > kPredTrust * (1.0 + fabs(cur.tm));
@@ -594,7 +594,7 @@ __device__ __forceinline__ void stab_lnK(const WS& ws, int64_t m, int t, double*
 #pragma unroll
     for (int i = 0; i < NC; i++) {
         lw[i] = ws.lnW[(t * NC + i) * n + m];
-        sw += exp(lw[i]);
+        sw += exp_fast(lw[i]);
     }
     const double ls = log(sw);
 #pragma unroll
@@ -705,7 +705,7 @@ struct SplitSS {
         if (maxabs<NC>(lnK) < kTrivialLnK) fail = 1;
         if (!fail) {
 #pragma unroll
-            for (int i = 0; i < NC; i++) K[i] = exp(lnK[i]);
+            for (int i = 0; i < NC; i++) K[i] = exp_fast(lnK[i]);
             if (!rachford_rice<NC>(z, K, th, t)) fail = 1;
         }
         if (!fail) {
@@ -1043,7 +1043,7 @@ __device__ __forceinline__ void stab_out_item(const CS& cs, const WS& ws, const 
             double lnK[NC];
             stab_lnK<NC>(ws, m, tl < tv ? 1 : 0, lnK);
 #pragma unroll
-            for (int i = 0; i < NC; i++) io.K[i * io.ld + m] = exp(lnK[i]);
+            for (int i = 0; i < NC; i++) io.K[i * io.ld + m] = exp_fast(lnK[i]);
             io.status[m] = st;
         }
     }
