@@ -44,6 +44,202 @@ __global__ void __launch_bounds__(kTile) k_nn_infer(MLP a, int nc, int64_t n, in
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core inference: each layer is a [samples x in] x [in x out] product,
+// run with the warp-level bf16 MMA (m16n8k16, FP32 accumulators).  A block of
+// 256 threads takes 128 samples per round; each warp owns 16 of them (one
+// M tile), so the layers need only warp-level ordering.  All weights live in
+// shared memory as bf16 [out][in] rows (rounded from the FP32 master like the
+// compute copy), padded by 8 elements so that the fragment loads hit 32
+// different banks; activations are bf16 rows padded the same way.  Epilogues
+// apply bias, SiLU and the bf16 rounding of the scalar path (FP32 sums run in
+// another order).  arch 1 keeps [u | h] in one row: the output layer reads the
+// concatenation directly and each residual block updates h in place.
+// ---------------------------------------------------------------------------
+constexpr int kMmaTile = 128;    // samples per block round
+constexpr int kMmaThreads = 256;  // 8 warps x 16 samples
+constexpr int kUPad = 32;         // input features padded to two k-steps
+
+struct MmaGeom {
+    int nl;                // layers
+    int K[8], N[8];        // padded inner / output sizes per layer
+    int woff[8];           // bf16 element offset of each layer's weights
+    int boff[8];           // float offset of each layer's bias
+    int wtotal, btotal;
+    int rs, ts;            // row strides (bf16 elements) of the activation tiles
+    int act0, act1, act2;  // bf16 element offsets of the tiles
+    size_t bytes;
+};
+
+__host__ __device__ inline MmaGeom mma_geom(const MLP& a) {
+    MmaGeom g{};
+    const int H = a.hid, L = n_layers(a);
+    g.nl = L;
+    int w = 0, b = 0;
+    for (int l = 0; l < L; l++) {
+        const int nout = layer_out(a, l);
+        g.K[l] = l == 0 ? kUPad : (a.arch == 1 && l == 7 ? kUPad + H : H);
+        g.N[l] = (nout + 7) & ~7;
+        g.woff[l] = w;
+        g.boff[l] = b;
+        w += g.N[l] * (g.K[l] + 8);
+        b += g.N[l];
+    }
+    g.wtotal = w;
+    g.btotal = b;
+    if (a.arch == 1) {
+        g.rs = kUPad + H + 8;  // [u | h]
+        g.ts = H + 8;          // a_k
+        g.act0 = w;
+        g.act1 = w + kMmaTile * g.rs;
+        g.act2 = g.act1 + kMmaTile * g.ts;
+    } else {
+        g.rs = kUPad + 8;      // u
+        g.ts = H + 8;          // two hidden tiles
+        g.act0 = w;
+        g.act1 = w + kMmaTile * g.rs;
+        g.act2 = g.act1 + kMmaTile * g.ts;
+    }
+    const int elems = g.act2 + (a.arch == 1 ? 0 : kMmaTile * g.ts);
+    g.bytes = (size_t)elems * 2 + (size_t)g.btotal * 4 + 16;
+    return g;
+}
+
+__device__ __forceinline__ uint32_t ld_u32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One layer for this warp's 16 rows: in (row stride sin, first column cin,
+// K columns) times W^T (N x K rows of stride K + 8) plus bias.  mode 0:
+// out = bf16(silu(.)) into tile (stride sout, column cout); mode 1: residual,
+// out = bf16(out + bf16(silu(.))); mode 2: FP32 to global y[o * ld + m].
+__device__ __forceinline__ void mma_layer(const __nv_bfloat16* in, int sin, int cin, int K, const __nv_bfloat16* W,
+                                          const float* bias, int N, int nreal, __nv_bfloat16* out, int sout,
+                                          int cout, int mode, float* y, int64_t ld, int64_t m0, int64_t n) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int ws = K + 8;
+    for (int n0 = 0; n0 < N; n0 += 32) {
+        float acc[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+        for (int k0 = 0; k0 < K; k0 += 16) {
+            uint32_t af[4];
+            const __nv_bfloat16* ar = in + g * sin + cin + k0 + 2 * t;
+            af[0] = ld_u32(ar);
+            af[1] = ld_u32(ar + 8 * sin);
+            af[2] = ld_u32(ar + 8);
+            af[3] = ld_u32(ar + 8 * sin + 8);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int nb = n0 + 8 * j;
+                if (nb < N) {
+                    const __nv_bfloat16* br = W + (nb + g) * ws + k0 + 2 * t;
+                    mma_bf16(acc[j], af, ld_u32(br), ld_u32(br + 8));
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int nb = n0 + 8 * j;
+            if (nb >= N) continue;
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const int row = g + (v >> 1) * 8, col = nb + 2 * t + (v & 1);
+                if (col >= nreal) continue;
+                const float pre = acc[j][v] + bias[col];
+                if (mode == 2) {
+                    const int64_t m = m0 + row;
+                    if (m < n) y[col * ld + m] = pre;
+                } else {
+                    float h = bf16_round(pre * sigmoidf_(pre));
+                    __nv_bfloat16* o = out + row * sout + cout + col;
+                    if (mode == 1) h = bf16_round(__bfloat162float(*o) + h);
+                    *o = __float2bfloat16_rn(h);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kMmaThreads, 1) k_nn_infer_mma(MLP a, int nc, int64_t n, int64_t ld, const double* P,
+                                                                const double* T, const double* z, float* out,
+                                                                int64_t out_ld) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __nv_bfloat16* sm = reinterpret_cast<__nv_bfloat16*>(smraw);
+    const MmaGeom G = mma_geom(a);
+    float* sb = reinterpret_cast<float*>(smraw + (size_t)(G.act2 + (a.arch == 1 ? 0 : kMmaTile * G.ts)) * 2);
+    // weights: bf16 [N][K + 8] from the FP32 master, zero padding; biases
+    for (int l = 0; l < G.nl; l++) {
+        const int nin = layer_in(a, l), nout = layer_out(a, l), ws = G.K[l] + 8;
+        const float* Wl = a.theta + theta_W(a, l);
+        const float* bl = a.theta + theta_b(a, l);
+        for (int e = threadIdx.x; e < G.N[l] * ws; e += blockDim.x) {
+            const int o = e / ws, kk = e - o * ws;
+            int k = -1;  // source column
+            if (a.arch == 1 && l == 7) k = kk < a.din ? kk : (kk >= kUPad && kk < kUPad + a.hid ? a.din + kk - kUPad : -1);
+            else if (kk < nin) k = kk;
+            const float v = (o < nout && k >= 0) ? Wl[o * nin + k] : 0.0f;
+            sm[G.woff[l] + e] = __float2bfloat16_rn(v);
+        }
+        for (int e = threadIdx.x; e < G.N[l]; e += blockDim.x) sb[G.boff[l] + e] = e < nout ? bl[e] : 0.0f;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __nv_bfloat16* R = sm + G.act0;     // u (arch 0) or [u | h] (arch 1)
+    __nv_bfloat16* A1 = sm + G.act1;
+    __nv_bfloat16* A2 = sm + G.act2;
+    const int r0 = warp * 16;
+    for (int64_t base = (int64_t)blockIdx.x * kMmaTile; base < n; base += (int64_t)gridDim.x * kMmaTile) {
+        // features of this warp's 16 samples: two lanes per sample
+        for (int e = lane; e < 16 * kUPad; e += 32) {
+            const int row = e / kUPad, i = e - row * kUPad;
+            const int64_t m = base + r0 + row;
+            float v = 0.0f;
+            if (m < n && i < a.din) {
+                const double x = i < nc ? z[i * ld + m] : (i == nc ? P[m] : T[m]);
+                v = ((float)x - __ldg(a.mean + i)) * __ldg(a.rstd + i);
+            }
+            R[(r0 + row) * G.rs + i] = __float2bfloat16_rn(v);
+        }
+        __syncwarp();
+        const int64_t m0 = base + r0;
+        if (a.arch == 0) {
+            mma_layer(R + r0 * G.rs, G.rs, 0, G.K[0], sm + G.woff[0], sb + G.boff[0], G.N[0], a.hid,
+                      A1 + r0 * G.ts, G.ts, 0, 0, nullptr, 0, 0, 0);
+            __syncwarp();
+            mma_layer(A1 + r0 * G.ts, G.ts, 0, G.K[1], sm + G.woff[1], sb + G.boff[1], G.N[1], a.hid,
+                      A2 + r0 * G.ts, G.ts, 0, 0, nullptr, 0, 0, 0);
+            __syncwarp();
+            mma_layer(A2 + r0 * G.ts, G.ts, 0, G.K[2], sm + G.woff[2], sb + G.boff[2], G.N[2], a.hid,
+                      A1 + r0 * G.ts, G.ts, 0, 0, nullptr, 0, 0, 0);
+            __syncwarp();
+            mma_layer(A1 + r0 * G.ts, G.ts, 0, G.K[3], sm + G.woff[3], sb + G.boff[3], G.N[3], a.dout,
+                      nullptr, 0, 0, 2, out, out_ld, m0, n);
+        } else {
+            mma_layer(R + r0 * G.rs, G.rs, 0, G.K[0], sm + G.woff[0], sb + G.boff[0], G.N[0], a.hid,
+                      R + r0 * G.rs, G.rs, kUPad, 0, nullptr, 0, 0, 0);
+            __syncwarp();
+            for (int k = 1; k <= 3; k++) {
+                mma_layer(R + r0 * G.rs, G.rs, kUPad, G.K[2 * k - 1], sm + G.woff[2 * k - 1], sb + G.boff[2 * k - 1],
+                          G.N[2 * k - 1], a.hid, A1 + r0 * G.ts, G.ts, 0, 0, nullptr, 0, 0, 0);
+                __syncwarp();
+                mma_layer(A1 + r0 * G.ts, G.ts, 0, G.K[2 * k], sm + G.woff[2 * k], sb + G.boff[2 * k], G.N[2 * k],
+                          a.hid, R + r0 * G.rs, G.rs, kUPad, 1, nullptr, 0, 0, 0);
+                __syncwarp();
+            }
+            mma_layer(R + r0 * G.rs, G.rs, 0, G.K[7], sm + G.woff[7], sb + G.boff[7], G.N[7], a.dout, nullptr, 0, 0,
+                      2, out, out_ld, m0, n);
+        }
+        __syncwarp();
+    }
+}
+
 // Standardised bf16 features X[i][m] (row stride n).
 __global__ void k_nn_features(MLP a, int nc, int64_t n, int64_t ld, const double* P, const double* T,
                               const double* z, float* X) {
@@ -345,6 +541,23 @@ namespace ptf {
 // Launch network inference for the flash pipeline (declared in ptf_mlp.cuh).
 cudaError_t nn_infer_launch(const MLP& a, int nc, int64_t n, int64_t ld, const double* P, const double* T,
                             const double* z, float* out, int64_t out_ld, int sms, cudaStream_t s) {
+    const MmaGeom G = mma_geom(a);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_nn_infer_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        attr = true;
+    }
+    if (G.bytes > 220 * 1024) return cudaErrorInvalidValue;
+    const int64_t tiles = (n + kMmaTile - 1) / kMmaTile;
+    const int grid = (int)(tiles < (int64_t)sms ? tiles : (int64_t)sms);
+    k_nn_infer_mma<<<grid > 0 ? grid : 1, kMmaThreads, G.bytes, s>>>(a, nc, n, ld, P, T, z, out, out_ld);
+    return cudaGetLastError();
+}
+
+// The scalar forward pass (one thread per sample, FP32 sums in input order),
+// kept beside the tensor-core one for the comparison test.
+cudaError_t nn_infer_scalar_launch(const MLP& a, int nc, int64_t n, int64_t ld, const double* P, const double* T,
+                                   const double* z, float* out, int64_t out_ld, int sms, cudaStream_t s) {
     const size_t sm = infer_smem(a);
     static bool attr = false;
     if (!attr) {

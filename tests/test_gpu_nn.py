@@ -130,6 +130,41 @@ def test_paper_network_gradients_match_oracle(ptf, oracle_mod, which, arch, hidd
     fl.close()
 
 
+@pytest.mark.parametrize("which,arch,hidden", [(0, 0, 32), (0, 0, 64), (1, 0, 128), (1, 1, 64)])
+def test_tensor_core_inference_matches_oracle(ptf, oracle_mod, which, arch, hidden):
+    """The inference kernel (warp-level bf16 MMA, FP32 accumulators) against
+    the FP64 network oracle on the same bf16 features: the sums differ only in
+    order, so outputs agree to FP32 rounding except where it tips a bf16
+    rounding of an activation."""
+    import torch
+    from oracle import mlp
+    comp, cond = wl.workload("nc10_2phase_1e6", 3000)  # not a multiple of the 128-sample tile
+    nc, n = comp.nc, cond.n
+    fl = ptf.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=4096)
+    dout = 1 if which == 0 else nc
+    rng = np.random.default_rng(33 + hidden + arch)
+    theta = mlp.init_params(nc + 2, hidden, dout, rng, arch=arch)
+    theta = (theta + rng.normal(0, 0.05, theta.shape)).astype(np.float32)
+    mean, std = (np.r_[cond.z.mean(1), cond.P.mean(), cond.T.mean()].astype(np.float32),
+                 np.r_[cond.z.std(1), cond.P.std(), cond.T.std()].astype(np.float32))
+    fl.ptflash_nn_set(which, hidden, theta, mean, std, arch=arch)
+    P, T, z = (torch.tensor(a, device="cuda") for a in (cond.P, cond.T, cond.z))
+    z = z.contiguous()
+    X = torch.empty(nc + 2, n, dtype=torch.float32, device="cuda")
+    fl.ptflash_nn_features(which, P, T, z, X)
+    out = torch.empty(dout, n, dtype=torch.float32, device="cuda")
+    fl.ptflash_nn_infer(which, P, T, z, out)
+    torch.cuda.synchronize()
+    ref, _ = mlp.forward(theta.astype(np.float64), X.cpu().numpy().T.astype(np.float64), nc + 2, hidden, dout, arch)
+    got = out.cpu().numpy().T
+    err = np.abs(got - ref)
+    scale = max(1.0, np.abs(ref).max())
+    print("inference", which, arch, hidden, "max err", err.max(), "mean", err.mean(), "scale", scale)
+    assert err.max() <= 5e-2 * scale and err.mean() <= 2e-3 * scale
+    assert np.quantile(err, 0.99) <= 1e-2 * scale
+    fl.close()
+
+
 def test_training_and_learned_flash_parity(ptf, oracle_mod):
     import torch
     from paper_2205_03090_gb300 import nn
