@@ -163,11 +163,15 @@ __device__ __forceinline__ void wilson(const Comp<NC>& cp, double P, double T, d
 // from the values of f at its critical points.  One root is found by Halley
 // iterations (Eq. halley) kept inside the sign-change bracket (bisection when
 // a step leaves it, so the iteration cannot stall at an extremum): an FP32
-// run seeds the FP64 run, which stops once a Halley step is below 1e-8
-// relative (Appendix A).  With three real roots, deflation (Appendix A) gives
-// the other two, each polished by one FP64 Newton step on the original cubic.
-// Among admissible roots the smallest and the largest are compared by the
-// residual Gibbs energy gbar(Z) = Z - 1 - ln(Z - B) - (A/B) ln(1 + B/Z).
+// run seeds the FP64 run.  The FP64 run stops after a Halley step below 2e-6
+// relative: Halley's cubic convergence leaves an error of order (2e-6)^3,
+// far below what the paper's 1e-8 step criterion (Appendix A) guarantees.
+// With three real roots, deflation (Appendix A) gives the other two.  Among
+// admissible roots the smallest and the largest are compared by the residual
+// Gibbs energy gbar(Z) = Z - 1 - ln(Z - B) - (A/B) ln(1 + B/Z): in FP32 when
+// the two differ by more than 1e-4 (FP32 rounding is below 1e-5 here), else
+// in FP64 after one FP64 Newton polish of both.  The chosen root gets that
+// polish and its FP64 logarithms.
 // ---------------------------------------------------------------------------
 struct Root {
     double Z, lzb, L;  // chosen root, ln(Z - B), ln(1 + B/Z)
@@ -175,6 +179,10 @@ struct Root {
 
 __device__ __forceinline__ double cub_f(double Z, double r1, double r0) { return fma(fma(Z - 1.0, Z, r1), Z, -r0); }
 __device__ __forceinline__ double cub_df(double Z, double r1) { return fma(fma(3.0, Z, -2.0), Z, r1); }
+__device__ __forceinline__ double cub_polish(double Z, double r1, double r0) {
+    const double d = cub_df(Z, r1);
+    return d != 0.0 ? Z - cub_f(Z, r1, r0) / d : Z;
+}
 
 __device__ __forceinline__ Root cubic_select(double A, double B) {
     const double r1 = A - B * (1.0 + B), r0 = A * B;
@@ -215,7 +223,7 @@ __device__ __forceinline__ Root cubic_select(double A, double B) {
         double fp = cub_df(z0, r1);
         double fpp = fma(6.0, z0, -2.0);
         double zn = z0 - 2.0 * f * fp / (2.0 * fp * fp - f * fpp);
-        if (fabs(zn - z0) <= 1e-8 * fabs(zn)) {  // converged (Appendix A criterion)
+        if (fabs(zn - z0) <= 2e-6 * fabs(zn)) {  // converged: accept before any bracket test
             z0 = zn;
             break;
         }
@@ -226,34 +234,40 @@ __device__ __forceinline__ Root cubic_select(double A, double B) {
         }
         z0 = zn;
     }
-    double zl = z0, zv = z0;
+    double z = z0;
     if (three) {
         // deflation: f = (Z - z0)(Z^2 + p Z + q), p = z0 - 1, q = p z0 + r1
         const double p = z0 - 1.0, q = fma(p, z0, r1);
         const double sd = sqrt(fmax(p * p - 4.0 * q, 0.0));
         const double t = -0.5 * (p + copysign(sd, p));  // stable quadratic roots
         const double q1 = t, q2 = (t != 0.0) ? q / t : t;
-        zl = fmin(z0, fmin(q1, q2));
-        zv = fmax(z0, fmax(q1, q2));
-        const double dl = cub_df(zl, r1), dv = cub_df(zv, r1);
-        if (dl != 0.0) zl -= cub_f(zl, r1, r0) / dl;
-        if (dv != 0.0) zv -= cub_f(zv, r1, r0) / dv;
+        double zl = fmin(z0, fmin(q1, q2)), zv = fmax(z0, fmax(q1, q2));
+        bool low = false;
+        if (zl > B && zl < zv) {
+            const float Bf = (float)B, ABf = (float)(A / B), zlf = (float)zl, zvf = (float)zv;
+            const float dg = (zlf - zvf) - (logf(zlf - Bf) - logf(zvf - Bf)) -
+                             ABf * (logf(1.0f + Bf / zlf) - logf(1.0f + Bf / zvf));
+            if (fabsf(dg) > 1e-4f) {
+                low = dg < 0.0f;
+            } else {
+                zl = cub_polish(zl, r1, r0);
+                zv = cub_polish(zv, r1, r0);
+                if (zl > B && zl < zv) {
+                    const double AB = A / B;
+                    const double gl = zl - log_fast(zl - B) - AB * log_fast(1.0 + B / zl);
+                    const double gv = zv - log_fast(zv - B) - AB * log_fast(1.0 + B / zv);
+                    low = gl < gv;
+                }
+                z = low ? zl : zv;
+                three = false;  // polished already
+            }
+        }
+        if (three) z = cub_polish(low ? zl : zv, r1, r0);
     }
     Root r;
-    const double lzbv = log_fast(zv - B), Lv = log_fast(1.0 + B / zv);
-    r.Z = zv;
-    r.lzb = lzbv;
-    r.L = Lv;
-    if (zl > B && zl < zv) {
-        const double lzbl = log_fast(zl - B), Ll = log_fast(1.0 + B / zl);
-        const double AB = A / B;
-        const double gl = zl - lzbl - AB * Ll, gv = zv - lzbv - AB * Lv;
-        if (gl < gv) {
-            r.Z = zl;
-            r.lzb = lzbl;
-            r.L = Ll;
-        }
-    }
+    r.Z = z;
+    r.lzb = log_fast(z - B);
+    r.L = log_fast(1.0 + B / z);
     return r;
 }
 
