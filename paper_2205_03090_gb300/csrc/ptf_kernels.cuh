@@ -509,9 +509,10 @@ struct StabTR {
         ws.tflag[t * n + m] = (fl & 0xff) | (iters << 8) | (1 << 16) | (maxiter << 17) | (nonfinite << 18);
     }
 
-    // 0 continue, 1 done
+    // 0 continue, 1 done.  tail: the queue is exhausted, so the lane runs the
+    // whole shift iteration in this trip (the same iterates either way).
     template <class CS>
-    __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io) {
+    __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io, bool tail) {
         const Comp<NC>& cp = cs.of(m);
         StabPt<NC> nxt;
         double u[NC], pred = 0.0;
@@ -520,9 +521,15 @@ struct StabTR {
             for (int i = 0; i < NC; i++) nxt.lnW[i] = cur.lnW[i];
         } else {
             double Lf[NC * (NC + 1) / 2];
-            // one shift per trip: few stability solves need more than one, and
-            // those lanes skip this trip's evaluation instead of holding the warp
-            if (tr_shift_step<NC>(cur.H, cur.g, radius, eta_lo, false, sh, Lf, u) == 0) return 0;
+            // one shift per trip while the queue lasts: few stability solves
+            // need more than one, and those lanes skip this trip's evaluation
+            // instead of holding the warp.  Once it is exhausted the slowest
+            // runs set the kernel's length, and a lane takes all its shifts.
+            int r = 0;
+#pragma unroll 1
+            for (int k = 0; k < (tail ? kTRShiftCap + 2 : 1) && r == 0; k++)
+                r = tr_shift_step<NC>(cur.H, cur.g, radius, eta_lo, false, sh, Lf, u);
+            if (r == 0) return 0;
             for (int i = 0; i < NC; i++) {
                 double hd = 0.0;
                 for (int j = 0; j < NC; j++) hd = fma(cur.H[i >= j ? tri(i, j) : tri(j, i)], u[j], hd);
@@ -580,7 +587,7 @@ __global__ void __launch_bounds__(128) k_stab_tr(const __grid_constant__ CS cs, 
             have = true;
         }
         if (!__any_sync(0xffffffffu, have)) break;
-        if (have && s.step(cs, ws, io)) have = false;
+        if (have && s.step(cs, ws, io, drained)) have = false;
     }
 }
 
