@@ -29,7 +29,7 @@ struct WS {
     double* tm;        // [2 n]
     int32_t* tflag;    // [2 n]: ss iters | tr iters << 8 | used_tr << 16 | maxiter << 17 | nonfinite << 18
     int32_t *q_stab, *q_split, *q_stab_tr, *q_split_tr;
-    int32_t* cnt;      // [0] stab, [1] split, [2] stab_tr (items), [3] split_tr
+    int32_t* cnt;      // [0] stab, [1] split, [2] stab_tr (items), [3] split_tr (all), [4] split_tr (first part)
     float* nnp = nullptr;  // learned form: classifier logits [n]
     float* nnk = nullptr;  // learned form: initializer ln K [NC n]
 };
@@ -45,7 +45,13 @@ struct IO {
 
 // ws.cnt slots: append counters of the queues, and read heads of the
 // persistent (refill) kernels
-enum { Q_STAB = 0, Q_SPLIT = 1, Q_STAB_TR = 2, Q_SPLIT_TR = 3 };
+enum { Q_STAB = 0, Q_SPLIT = 1, Q_STAB_TR = 2, Q_SPLIT_TR = 3, Q_SPLIT_TR_SLOW = 4, Q_SPLIT_TR_FAST = 5 };
+// Split TR queue order: the runs whose last SS updates contracted slowly
+// (ratio above kSlowSS) are expected to need the most trust-region steps;
+// they fill the queue from the front and the others from the back, so that
+// the longest runs start first and the kernel's tail shortens.  Only the
+// order of the work changes.
+constexpr double kSlowSS = 0.3;
 enum { H_PRE = 8, H_STAB = 9, H_STAB_TR = 10, H_SPLIT = 11, H_SPLIT_TR = 12 };
 
 // Component data of a launch.  OneSys: one fluid system, a kernel parameter
@@ -72,6 +78,30 @@ __device__ __forceinline__ void warp_append(int32_t* cnt, int32_t* queue, bool p
     if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (pred) queue[base + __popc(m & ((1u << lane) - 1u))] = value;
+}
+
+// Append to a queue of capacity cap filled from both ends: slow = true at
+// the front (counter *cs), else at the back (counter *cb, entry k at
+// cap - 1 - k); *ct counts both.  Every lane of the warp must call it.
+__device__ __forceinline__ void warp_append2(int32_t* ct, int32_t* cs, int32_t* cb, int32_t* queue, int64_t cap,
+                                             bool pred, bool slow, int32_t value) {
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (!m) return;
+    const unsigned ms = __ballot_sync(0xffffffffu, pred && slow), mb = m & ~ms;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int bs = 0, bb = 0;
+    if (lane == 0) {
+        atomicAdd(ct, __popc(m));
+        if (ms) bs = atomicAdd(cs, __popc(ms));
+        if (mb) bb = atomicAdd(cb, __popc(mb));
+    }
+    bs = __shfl_sync(0xffffffffu, bs, 0);
+    bb = __shfl_sync(0xffffffffu, bb, 0);
+    if (pred) {
+        if (slow) queue[bs + __popc(ms & lt)] = value;
+        else queue[cap - 1 - (bb + __popc(mb & lt))] = value;
+    }
 }
 
 // Refill for persistent kernels: the lanes that need work (need = true) take
@@ -700,7 +730,8 @@ struct SplitSS {
         if (io.iters) io.iters[m] = (io.iters[m] & ~0xff) | (iters & 0xff);
     }
 
-    // 0 continue, 1 done, 2 needs the trust region
+    // 0 continue, 1 done, 2 needs the trust region, 3 needs it and converged
+    // slowly in SS
     template <class CS>
     __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io) {
         const Comp<NC>& cp = cs.of(m);
@@ -764,7 +795,7 @@ struct SplitSS {
             for (int i = 0; i < NC; i++)
                 ws.nV[i * n + m] = inside ? th * y[i] : 0.5 * K[i] * z[i] / (1.0 + 0.5 * (K[i] - 1.0));
             finish(io, ST_SPLIT_TR);
-            return 2;
+            return res > kSlowSS * maxabs<NC>(dp) ? 3 : 2;
         }
         double dk[NC];
 #pragma unroll
@@ -805,7 +836,8 @@ __global__ void __launch_bounds__(128) k_split_ss(const __grid_constant__ CS cs,
         }
         if (!__any_sync(0xffffffffu, have)) break;
         const int r = have ? s.step(cs, ws, io) : 0;
-        warp_append(ws.cnt + Q_SPLIT_TR, ws.q_split_tr, r == 2, (int32_t)s.m);
+        warp_append2(ws.cnt + Q_SPLIT_TR, ws.cnt + Q_SPLIT_TR_SLOW, ws.cnt + Q_SPLIT_TR_FAST, ws.q_split_tr, ws.n,
+                     r >= 2, r == 3, (int32_t)s.m);
         if (r) have = false;
     }
 }
@@ -1015,12 +1047,13 @@ struct SplitTR {
 template <int NC, class CS>
 __global__ void __launch_bounds__(128) k_split_tr(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_SPLIT_TR);
+    const int64_t slow = *(volatile int32_t*)(ws.cnt + Q_SPLIT_TR_SLOW);
     SplitTR<NC> s;
     bool have = false, drained = false;
     for (;;) {
         const int64_t pos = warp_fetch(ws.cnt + H_SPLIT_TR, !have, len, drained);
         if (pos >= 0) {
-            s.begin(cs, ws, io, ws.q_split_tr[pos]);
+            s.begin(cs, ws, io, ws.q_split_tr[pos < slow ? pos : ws.n - 1 - (pos - slow)]);
             have = true;
         }
         if (!__any_sync(0xffffffffu, have)) break;
