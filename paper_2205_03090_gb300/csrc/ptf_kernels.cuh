@@ -294,9 +294,12 @@ struct PrecheckSS {
 };
 
 // Persistent kernel: lanes whose mixture finished take the next one, so the
-// warp keeps all lanes busy until the batch is exhausted.
+// warp keeps all lanes busy until the batch is exhausted.  Three resident
+// blocks per SM (168 registers, the rest spilled): the extra warps hide more
+// FP64 latency than the spills cost (also for split SS and split TR; the
+// stability TR kernel is no faster that way).
 template <int NC, class CS>
-__global__ void __launch_bounds__(128) k_precheck(const __grid_constant__ CS cs, WS ws, IO io) {
+__global__ void __launch_bounds__(128, 3) k_precheck(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = ws.n;
     PrecheckSS<NC> s;
     bool have = false, drained = false;
@@ -824,7 +827,7 @@ struct SplitSS {
 };
 
 template <int NC, class CS>
-__global__ void __launch_bounds__(128) k_split_ss(const __grid_constant__ CS cs, WS ws, IO io) {
+__global__ void __launch_bounds__(128, 3) k_split_ss(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_SPLIT);
     SplitSS<NC> s;
     bool have = false, drained = false;
@@ -1045,7 +1048,7 @@ struct SplitTR {
 };
 
 template <int NC, class CS>
-__global__ void __launch_bounds__(128) k_split_tr(const __grid_constant__ CS cs, WS ws, IO io) {
+__global__ void __launch_bounds__(128, 3) k_split_tr(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_SPLIT_TR);
     const int64_t slow = *(volatile int32_t*)(ws.cnt + Q_SPLIT_TR_SLOW);
     SplitTR<NC> s;
