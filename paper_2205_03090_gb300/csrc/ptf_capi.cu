@@ -25,9 +25,11 @@ int cuda_fail(cudaError_t e) {
     } while (0)
 }  // namespace
 
-// Fold the four queue counters of a chunk into the call's accumulator.
+// Fold the four queue counters of a chunk into the call's accumulator (the
+// split queue is counted from both of its ends).
 __global__ void k_fold_counts(const int32_t* cnt, unsigned long long* acc) {
-    if (threadIdx.x < 4) acc[threadIdx.x] += (unsigned long long)cnt[threadIdx.x];
+    if (threadIdx.x < 4)
+        acc[threadIdx.x] += (unsigned long long)cnt[threadIdx.x] + (threadIdx.x == Q_SPLIT ? cnt[Q_SPLIT_B] : 0);
 }
 
 static cudaError_t dispatch(ptflash_ctx* c, const WS& ws, const IO& io, int mode, cudaStream_t s, float p_l = 0.02f,
@@ -41,7 +43,7 @@ static cudaError_t dispatch(ptflash_ctx* c, const WS& ws, const IO& io, int mode
     }
     switch (c->comp.nc) {
 #define PTF_CASE(NC) \
-    case NC: return launch_plain<NC>(c->comp, ws, io, grid, mode, s, ev, nn, p_l, p_r);
+    case NC: return launch_plain<NC>(c->comp, ws, io, grid, mode, s, ev, nn, p_l, p_r, c->conc.hi ? &c->conc : nullptr);
         PTF_CASE(2) PTF_CASE(3) PTF_CASE(4) PTF_CASE(5) PTF_CASE(6) PTF_CASE(7) PTF_CASE(8) PTF_CASE(9)
         PTF_CASE(10) PTF_CASE(11) PTF_CASE(12) PTF_CASE(13) PTF_CASE(14) PTF_CASE(15) PTF_CASE(16)
 #undef PTF_CASE
@@ -134,6 +136,19 @@ int ptflash_create(ptflash_ctx** out, int nc_max, int64_t n_max) {
         delete c;
         return PTF_ERR_NO_MEMORY;
     }
+    // streams of the concurrent split SS: the stability chain at the highest
+    // priority, the independent split SS at the lowest
+    int lo = 0, hi = 0;
+    bool ok = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&c->conc.hi, cudaStreamNonBlocking, hi) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&c->conc.lo, cudaStreamNonBlocking, lo) == cudaSuccess;
+    for (cudaEvent_t* e : {&c->conc.fork, &c->conc.pre, &c->conc.lo_done, &c->conc.hi_done})
+        ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        ptflash_destroy(c);
+        return PTF_ERR_CUDA;
+    }
     *out = c;
     return PTF_OK;
 }
@@ -141,6 +156,10 @@ int ptflash_create(ptflash_ctx** out, int nc_max, int64_t n_max) {
 int ptflash_destroy(ptflash_ctx* c) {
     if (!c) return PTF_ERR_INVALID_ARG;
     cudaDeviceSynchronize();
+    if (c->conc.hi) cudaStreamDestroy(c->conc.hi);
+    if (c->conc.lo) cudaStreamDestroy(c->conc.lo);
+    for (cudaEvent_t e : {c->conc.fork, c->conc.pre, c->conc.lo_done, c->conc.hi_done})
+        if (e) cudaEventDestroy(e);
     cudaFree(c->wsd);
     cudaFree(c->wsi);
     cudaFree(c->hd);

@@ -48,6 +48,7 @@ struct ptflash_ctx {
     float* train_scratch = nullptr;
     size_t train_scratch_bytes = 0;
     bool profiling = false;
+    Conc conc;  // streams and events of the concurrent split SS (flash calls without profiling)
     cudaEvent_t ev[kStages + 1] = {};
     double stage_ms[kStages] = {};
 };

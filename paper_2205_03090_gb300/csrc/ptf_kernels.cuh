@@ -29,7 +29,7 @@ struct WS {
     double* tm;        // [2 n]
     int32_t* tflag;    // [2 n]: ss iters | tr iters << 8 | used_tr << 16 | maxiter << 17 | nonfinite << 18
     int32_t *q_stab, *q_split, *q_stab_tr, *q_split_tr;
-    int32_t* cnt;      // [0] stab, [1] split, [2] stab_tr (items), [3] split_tr (all), [4] split_tr (first part)
+    int32_t* cnt;      // queue counters and read heads (enums below)
     float* nnp = nullptr;  // learned form: classifier logits [n]
     float* nnk = nullptr;  // learned form: initializer ln K [NC n]
 };
@@ -45,14 +45,19 @@ struct IO {
 
 // ws.cnt slots: append counters of the queues, and read heads of the
 // persistent (refill) kernels
-enum { Q_STAB = 0, Q_SPLIT = 1, Q_STAB_TR = 2, Q_SPLIT_TR = 3, Q_SPLIT_TR_SLOW = 4, Q_SPLIT_TR_FAST = 5 };
+// The split queue q_split is filled from both ends: from the front by the
+// precheck (or the classifier gate), counter Q_SPLIT; from the back by the
+// stability decision, counter Q_SPLIT_B (entry k at n - 1 - k).  The two parts
+// do not depend on each other, so their split SS can run concurrently.
+enum { Q_STAB = 0, Q_SPLIT = 1, Q_STAB_TR = 2, Q_SPLIT_TR = 3, Q_SPLIT_TR_SLOW = 4, Q_SPLIT_TR_FAST = 5,
+       Q_SPLIT_B = 6 };
 // Split TR queue order: the runs whose last SS updates contracted slowly
 // (ratio above kSlowSS) are expected to need the most trust-region steps;
 // they fill the queue from the front and the others from the back, so that
 // the longest runs start first and the kernel's tail shortens.  Only the
 // order of the work changes.
 constexpr double kSlowSS = 0.3;
-enum { H_PRE = 8, H_STAB = 9, H_STAB_TR = 10, H_SPLIT = 11, H_SPLIT_TR = 12 };
+enum { H_PRE = 8, H_STAB = 9, H_STAB_TR = 10, H_SPLIT = 11, H_SPLIT_TR = 12, H_SPLIT_B = 13 };
 
 // Component data of a launch.  OneSys: one fluid system, a kernel parameter
 // read through the constant bank.  ManySys: several systems of the same nc (a
@@ -78,6 +83,17 @@ __device__ __forceinline__ void warp_append(int32_t* cnt, int32_t* queue, bool p
     if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (pred) queue[base + __popc(m & ((1u << lane) - 1u))] = value;
+}
+
+// Warp-aggregated append at the back of a queue of capacity cap (entry k at
+// cap - 1 - k).  Every lane of the warp must call it.
+__device__ __forceinline__ void warp_append_back(int32_t* cnt, int32_t* queue, int64_t cap, bool pred, int32_t value) {
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (pred) queue[cap - 1 - (base + __popc(m & ((1u << lane) - 1u)))] = value;
 }
 
 // Append to a queue of capacity cap filled from both ends: slow = true at
@@ -108,15 +124,25 @@ __device__ __forceinline__ void warp_append2(int32_t* ct, int32_t* cs, int32_t* 
 // the next positions of a queue whose read head is *head; returns this lane's
 // position, or -1 if it needs none or the queue is exhausted.  Every lane of
 // the warp must call it.  `drained` (warp-uniform) stops further atomics.
-__device__ __forceinline__ int64_t warp_fetch(int32_t* head, bool need, int64_t len, bool& drained) {
+__device__ __forceinline__ int64_t warp_fetch(int32_t* head, bool need, int64_t len, bool& drained,
+                                              int* blk_taken = nullptr, int quota = 0) {
     const unsigned m = __ballot_sync(0xffffffffu, need);
     const int lane = threadIdx.x & 31;
     int64_t base = len;
     if (m && !drained) {
         int b = 0;
-        if (lane == 0) b = atomicAdd(head, __popc(m));
-        base = __shfl_sync(0xffffffffu, b, 0);
-        if (base + __popc(m) >= len) drained = true;  // this fetch reached the end
+        if (lane == 0) {
+            // a block with a quota stops fetching once its warps took that many items
+            if (quota > 0 && atomicAdd(blk_taken, __popc(m)) >= quota) b = -1;
+            else b = atomicAdd(head, __popc(m));
+        }
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b < 0) {
+            drained = true;
+        } else {
+            base = b;
+            if (base + __popc(m) >= len) drained = true;  // this fetch reached the end
+        }
     }
     const int64_t pos = base + __popc(m & ((1u << lane) - 1u));
     return (need && pos < len) ? pos : -1;
@@ -693,7 +719,7 @@ __global__ void __launch_bounds__(128) k_stab_decide(const __grid_constant__ CS 
     PTF_WARP_ROUNDS(len, qi, valid) {
         const int64_t m = valid ? ws.q_stab[qi] : 0;
         const bool to_split = valid ? stab_decide_item<NC>(cs, ws, io, m) : false;
-        warp_append(ws.cnt + Q_SPLIT, ws.q_split, to_split, (int32_t)m);
+        warp_append_back(ws.cnt + Q_SPLIT_B, ws.q_split, ws.n, to_split, (int32_t)m);
     }
 }
 
@@ -826,15 +852,25 @@ struct SplitSS {
     }
 };
 
+// part 0: the front of the split queue; 1: its back; 2: both.  quota > 0:
+// each block takes at most about `quota` items and exits (short blocks, so
+// that a concurrent higher-priority kernel gets SMs as they free up);
+// otherwise the kernel is persistent.
 template <int NC, class CS>
-__global__ void __launch_bounds__(128, 3) k_split_ss(const __grid_constant__ CS cs, WS ws, IO io) {
-    const int64_t len = *(volatile int32_t*)(ws.cnt + Q_SPLIT);
+__global__ void __launch_bounds__(128, 3) k_split_ss(const __grid_constant__ CS cs, WS ws, IO io, int part, int quota) {
+    const int64_t na = *(volatile int32_t*)(ws.cnt + Q_SPLIT), nb = *(volatile int32_t*)(ws.cnt + Q_SPLIT_B);
+    const int64_t len = part == 0 ? na : (part == 1 ? nb : na + nb);
+    const int64_t front = part == 1 ? 0 : na;  // positions below `front` read the front part
+    int32_t* head = ws.cnt + (part == 1 ? H_SPLIT_B : H_SPLIT);
+    __shared__ int blk_taken;
+    if (threadIdx.x == 0) blk_taken = 0;
+    __syncthreads();
     SplitSS<NC> s;
     bool have = false, drained = false;
     for (;;) {
-        const int64_t pos = warp_fetch(ws.cnt + H_SPLIT, !have, len, drained);
+        const int64_t pos = warp_fetch(head, !have, len, drained, &blk_taken, quota);
         if (pos >= 0) {
-            s.begin(cs, ws, io, ws.q_split[pos]);
+            s.begin(cs, ws, io, ws.q_split[pos < front ? pos : ws.n - 1 - (pos - front)]);
             have = true;
         }
         if (!__any_sync(0xffffffffu, have)) break;

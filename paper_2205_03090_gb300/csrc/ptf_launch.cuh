@@ -24,17 +24,32 @@ int persistent_grid(Kernel k, int sms) {
     return sms * b;
 }
 
+// Streams and events (owned by the caller) that let the split SS of the
+// mixtures the precheck (or the classifier gate) sends to the split run beside
+// the stability stages: those do not depend on stability analysis.  The
+// stability chain runs on the high-priority stream; the independent split SS
+// runs on the low-priority one in short blocks, which take the SMs the chain's
+// kernels leave idle as they drain.
+struct Conc {
+    cudaStream_t hi = nullptr, lo = nullptr;
+    cudaEvent_t fork = nullptr, pre = nullptr, lo_done = nullptr, hi_done = nullptr;
+};
+// Items per block of the low-priority split SS (4 per thread).
+constexpr int kFillerQuota = 512;
+
 // The flash pipeline over one workspace.  mode 0: plain flash; mode 1:
 // stability only; mode 2: learned form (nn = {classifier, initializer}, p_l /
 // p_r its thresholds).  ev (optional, kStages + 1 events) is recorded before
 // each stage and after the last one.  `grid` is the grid of the one-pass
 // kernels; the persistent kernels are sized to the device (sms = grid / 8),
 // or to `pgrid` blocks when it is positive.  CS is the component source
-// (OneSys or ManySys).
+// (OneSys or ManySys).  cc (optional, flash modes without stage events): run
+// the stages on cc's streams as described at Conc; the work is ordered after
+// what s holds and s waits for all of it.
 template <int NC, class CS>
 cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, int mode, cudaStream_t s,
                             cudaEvent_t* ev, const MLP* nn = nullptr, float p_l = 0.02f, float p_r = 0.98f,
-                            int pgrid = 0) {
+                            int pgrid = 0, const Conc* cc = nullptr) {
     const int sms = grid / 8 > 0 ? grid / 8 : 1;
     static const int g_pre = persistent_grid(k_precheck<NC, CS>, sms);
     static const int g_sss = persistent_grid(k_stab_ss<NC, CS>, sms);
@@ -45,6 +60,13 @@ cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, 
     auto mark = [&](int k) {
         if (ev) cudaEventRecord(ev[k], s);
     };
+    const bool conc = cc && !ev && mode != 1;
+    const cudaStream_t s0 = s;
+    if (conc) {
+        cudaEventRecord(cc->fork, s0);
+        cudaStreamWaitEvent(cc->hi, cc->fork, 0);
+        s = cc->hi;
+    }
     mark(0);
     if (mode == 0) {
         k_prep<NC, true, CS><<<grid, 128, 0, s>>>(cs, ws, io);
@@ -59,6 +81,13 @@ cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, 
         k_prep<NC, false, CS><<<grid, 128, 0, s>>>(cs, ws, io);
     }
     mark(1);
+    if (conc) {
+        cudaEventRecord(cc->pre, s);
+        cudaStreamWaitEvent(cc->lo, cc->pre, 0);
+        const int fg = (int)((ws.n + kFillerQuota - 1) / kFillerQuota);
+        k_split_ss<NC, CS><<<fg > 0 ? fg : 1, 128, 0, cc->lo>>>(cs, ws, io, 0, kFillerQuota);
+        cudaEventRecord(cc->lo_done, cc->lo);
+    }
     k_stab_ss<NC, CS><<<pg(g_sss), 128, 0, s>>>(cs, ws, io);
     mark(2);
     k_stab_tr<NC, CS><<<pg(g_str), 128, 0, s>>>(cs, ws, io);
@@ -67,7 +96,8 @@ cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, 
     else k_stab_out<NC, CS><<<grid, 128, 0, s>>>(cs, ws, io);
     mark(4);
     if (mode != 1) {
-        k_split_ss<NC, CS><<<pg(g_sps), 128, 0, s>>>(cs, ws, io);
+        k_split_ss<NC, CS><<<pg(g_sps), 128, 0, s>>>(cs, ws, io, conc ? 1 : 2, 0);
+        if (conc) cudaStreamWaitEvent(s, cc->lo_done, 0);
         mark(5);
         k_split_tr<NC, CS><<<pg(g_spt), 128, 0, s>>>(cs, ws, io);
         mark(6);
@@ -75,15 +105,20 @@ cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, 
         mark(5);
         mark(6);
     }
+    if (conc) {
+        cudaEventRecord(cc->hi_done, s);
+        cudaStreamWaitEvent(s0, cc->hi_done, 0);
+    }
     return cudaGetLastError();
 }
 
 // One fluid system (the component table as a kernel parameter).
 template <int NC>
 cudaError_t launch_plain(const CompHost& h, const WS& ws, const IO& io, int grid, int mode, cudaStream_t s,
-                         cudaEvent_t* ev, const MLP* nn = nullptr, float p_l = 0.02f, float p_r = 0.98f) {
+                         cudaEvent_t* ev, const MLP* nn = nullptr, float p_l = 0.02f, float p_r = 0.98f,
+                         const Conc* cc = nullptr) {
     const OneSys<NC> cs{make_comp<NC>(h)};
-    return launch_pipeline<NC>(cs, ws, io, grid, mode, s, ev, nn, p_l, p_r);
+    return launch_pipeline<NC>(cs, ws, io, grid, mode, s, ev, nn, p_l, p_r, 0, cc);
 }
 
 // Several systems of one nc over one workspace (a group of a batch): mode 0
@@ -98,7 +133,7 @@ cudaError_t launch_many(const Comp<NC>* tab, const int32_t* sys, const WS& ws, c
 // explicit instantiations live in ptf_inst_*.cu
 #define PTF_DECLARE_NC(NC)                                                                                      \
     extern template cudaError_t launch_plain<NC>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, \
-                                                 cudaEvent_t*, const MLP*, float, float);                        \
+                                                 cudaEvent_t*, const MLP*, float, float, const Conc*);           \
     extern template cudaError_t launch_many<NC>(const Comp<NC>*, const int32_t*, const WS&, const IO&, int, int, \
                                                 int, cudaStream_t);                                              \
     extern template cudaError_t launch_adjoint<NC>(const CompHost&, const AdjIO&, int, cudaStream_t);
@@ -110,7 +145,7 @@ PTF_DECLARE_NC(14) PTF_DECLARE_NC(15) PTF_DECLARE_NC(16)
 // Used once per NC by the instantiation units.
 #define PTF_INSTANTIATE_NC(NC)                                                                                    \
     template cudaError_t launch_plain<NC>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, cudaEvent_t*, \
-                                          const MLP*, float, float);                                               \
+                                          const MLP*, float, float, const Conc*);                                  \
     template cudaError_t launch_many<NC>(const Comp<NC>*, const int32_t*, const WS&, const IO&, int, int, int,     \
                                          cudaStream_t);                                                            \
     template cudaError_t launch_adjoint<NC>(const CompHost&, const AdjIO&, int, cudaStream_t);
