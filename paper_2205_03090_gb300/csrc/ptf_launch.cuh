@@ -34,8 +34,9 @@ struct Conc {
     cudaStream_t hi = nullptr, lo = nullptr;
     cudaEvent_t fork = nullptr, pre = nullptr, lo_done = nullptr, hi_done = nullptr;
 };
-// Items per block of the low-priority split SS (4 per thread).
-constexpr int kFillerQuota = 512;
+// Items per block of the low-priority split SS (2 per thread; 512 and more
+// measured slower).
+constexpr int kFillerQuota = 256;
 
 // The flash pipeline over one workspace.  mode 0: plain flash; mode 1:
 // stability only; mode 2: learned form (nn = {classifier, initializer}, p_l /
