@@ -381,6 +381,40 @@ __device__ __forceinline__ bool rachford_rice(const double* z, const double* K, 
     double km1[NC];
 #pragma unroll
     for (int i = 0; i < NC; i++) km1[i] = K[i] - 1.0;
+    {
+        // FP32 run of the same iteration from the same start: it seeds the
+        // FP64 run, which then needs about two steps (FP32 operations cost a
+        // small fraction of an FP64 one here)
+        const float alf = (float)al, arf = (float)ar;
+        float lof = alf, hif = arf, tf = (float)th;
+        float k1f[NC], zf[NC];
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            k1f[i] = (float)km1[i];
+            zf[i] = (float)z[i];
+        }
+#pragma unroll 1
+        for (int it = 0; it < 60; it++) {
+            float f = 0.0f, fp = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NC; i++) {
+                const float a = __fdividef(k1f[i], fmaf(k1f[i], tf, 1.0f));
+                f = fmaf(a, zf[i], f);
+                fp = fmaf(-a * a, zf[i], fp);
+            }
+            if (f > 0.0f) lof = tf; else hif = tf;
+            const float g1 = tf - alf, g2 = arf - tf;
+            const float tn = tf - (g1 * g2 * f) / ((g2 - g1) * f + g1 * g2 * fp);
+            if (fabsf(tn - tf) <= 1e-6f * fmaxf(1.0f, fabsf(tf))) {
+                tf = tn;
+                break;
+            }
+            tf = (tn > lof && tn < hif) ? tn : 0.5f * (lof + hif);
+            if (!(lof < hif)) break;
+        }
+        const double ts = (double)tf;
+        if (ts > lo && ts < hi) th = ts;
+    }
 #pragma unroll 1
     for (int it = 0; it < 200; it++) {
         double f = 0.0, fp = 0.0;
