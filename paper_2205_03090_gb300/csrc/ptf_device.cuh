@@ -186,18 +186,37 @@ __device__ __forceinline__ double cub_polish(double Z, double r1, double r0) {
 
 __device__ __forceinline__ Root cubic_select(double A, double B) {
     const double r1 = A - B * (1.0 + B), r0 = A * B;
-    // real-root count from the critical points of f (local max zm, local min zp)
+    // real-root count from the critical points of f (local max zm, local min
+    // zp).  They exist only for r1 < 1/3, where every term of f at them is
+    // below 2 in size: FP32 decides when both values are clear of zero by
+    // 1e-5 (FP32 rounding is below 1e-6 there), FP64 otherwise.
     bool three = false;
-    const double dcrit = 4.0 - 12.0 * r1;
-    if (dcrit > 0.0) {
-        const double sq = sqrt(dcrit);
-        const double fm = cub_f((2.0 - sq) * (1.0 / 6.0), r1, r0), fpv = cub_f((2.0 + sq) * (1.0 / 6.0), r1, r0);
-        three = !(fm < 0.0) && !(fpv > 0.0);
+    const float r1f = (float)r1, r0f = (float)r0;
+    const float dcf = fmaf(-12.0f, r1f, 4.0f);
+    if (dcf > -1e-5f) {
+        bool decided = false;
+        if (dcf > 1e-5f) {
+            const float sqf = sqrtf(dcf);
+            const float zmf = (2.0f - sqf) * (1.0f / 6.0f), zpf = (2.0f + sqf) * (1.0f / 6.0f);
+            const float fm = fmaf(fmaf(zmf - 1.0f, zmf, r1f), zmf, -r0f);
+            const float fpv = fmaf(fmaf(zpf - 1.0f, zpf, r1f), zpf, -r0f);
+            if (fabsf(fm) > 1e-5f && fabsf(fpv) > 1e-5f) {
+                three = fm > 0.0f && fpv < 0.0f;
+                decided = true;
+            }
+        }
+        if (!decided) {
+            const double dcrit = 4.0 - 12.0 * r1;
+            if (dcrit > 0.0) {
+                const double sq = sqrt(dcrit);
+                const double fm = cub_f((2.0 - sq) * (1.0 / 6.0), r1, r0), fpv = cub_f((2.0 + sq) * (1.0 / 6.0), r1, r0);
+                three = !(fm < 0.0) && !(fpv > 0.0);
+            }
+        }
     }
     // FP32 seed: bracketed Halley on (B, 1 + B]
     float lof = (float)B, hif = 1.0f + (float)B, zf = hif;
     {
-        const float r1f = (float)r1, r0f = (float)r0;
 #pragma unroll 1
         for (int it = 0; it < 40; it++) {
             float f = fmaf(fmaf(zf - 1.0f, zf, r1f), zf, -r0f);
