@@ -16,7 +16,10 @@ template <int NC>
 Comp<NC> make_comp(const CompHost& h) {
     Comp<NC> c;
     for (int i = 0; i < NC; i++) {
-        for (int j = 0; j < NC; j++) c.kk[i * NC + j] = 1.0 - h.kij[i * NC + j];
+        for (int j = 0; j < NC; j++) {
+            c.kk[i * NC + j] = 1.0 - h.kij[i * NC + j];
+            c.kkf[i * NC + j] = (float)c.kk[i * NC + j];
+        }
         c.Tc[i] = h.Tc[i];
         c.Pc[i] = h.Pc[i];
         c.lnPc[i] = std::log(h.Pc[i]);

@@ -56,6 +56,7 @@ template <int NC>
 struct Comp {
     double kk[NC * NC];  // 1 - k_ij
     double Tc[NC], Pc[NC], lnPc[NC], mi[NC], wc[NC];  // wc = 5.373 (1 + omega)
+    float kkf[NC * NC];  // 1 - k_ij in FP32 (the FP32 stability pre-iteration)
 };
 
 // ---------------------------------------------------------------------------
@@ -378,6 +379,75 @@ __device__ __forceinline__ void dlnphi_dn(const Comp<NC>& cp, const Mix<NC>& mx,
 }
 
 // ---------------------------------------------------------------------------
+// FP32 copy of the phase evaluation (Eqs. mixing_rule, cubic_Z, lnphi), used
+// only by the FP32 pre-iteration of stability analysis, whose iterates the
+// FP64 iteration then finishes: every decision and every reported number
+// comes from FP64.  Same steps as eos and cubic_select (bracketed Halley, root
+// count from the critical points, deflation, lower gbar), FP32 arithmetic and
+// intrinsics; ln(1 + B/Z) by log1pf (B/Z can be 1e-4).  Returns false on a
+// non-finite result.
+// ---------------------------------------------------------------------------
+template <int NC>
+__device__ __forceinline__ bool eos_f(const Comp<NC>& cp, const float* sA, const float* Bi, const float* c,
+                                     float* lnphi) {
+    float sc[NC], psi[NC], A = 0.0f, B = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NC; j++) sc[j] = sA[j] * c[j];
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        float acc = sc[i];
+#pragma unroll
+        for (int j = 0; j < NC; j++)
+            if (j != i) acc = fmaf(cp.kkf[i * NC + j], sc[j], acc);
+        psi[i] = sA[i] * acc;
+        A = fmaf(c[i], psi[i], A);
+        B = fmaf(c[i], Bi[i], B);
+    }
+    const float r1 = A - B * (1.0f + B), r0 = A * B;
+    float lo = B, hi = 1.0f + B, z = hi;
+#pragma unroll 1
+    for (int it = 0; it < 40; it++) {
+        const float f = fmaf(fmaf(z - 1.0f, z, r1), z, -r0);
+        if (f < 0.0f) lo = z; else hi = z;
+        const float fp = fmaf(fmaf(3.0f, z, -2.0f), z, r1), fpp = fmaf(6.0f, z, -2.0f);
+        float zn = z - __fdividef(2.0f * f * fp, 2.0f * fp * fp - f * fpp);
+        if (fabsf(zn - z) <= 1e-6f * z) {
+            z = zn;
+            break;
+        }
+        if (!(zn > lo && zn < hi)) zn = 0.5f * (lo + hi);
+        z = zn;
+    }
+    float Z = z;
+    const float dc = fmaf(-12.0f, r1, 4.0f);
+    if (dc > 0.0f) {
+        const float sq = sqrtf(dc);
+        const float zm = (2.0f - sq) * (1.0f / 6.0f), zp = (2.0f + sq) * (1.0f / 6.0f);
+        const float fm = fmaf(fmaf(zm - 1.0f, zm, r1), zm, -r0), fpv = fmaf(fmaf(zp - 1.0f, zp, r1), zp, -r0);
+        if (!(fm < 0.0f) && !(fpv > 0.0f)) {
+            const float p = z - 1.0f, q = fmaf(p, z, r1);
+            const float sd = sqrtf(fmaxf(p * p - 4.0f * q, 0.0f));
+            const float t = -0.5f * (p + copysignf(sd, p));
+            const float q1 = t, q2 = (t != 0.0f) ? q / t : t;
+            const float zl = fminf(z, fminf(q1, q2)), zv = fmaxf(z, fmaxf(q1, q2));
+            if (zl > B && zl < zv) {
+                const float AB = A / B;
+                const float gl = zl - __logf(zl - B) - AB * log1pf(B / zl);
+                const float gv = zv - __logf(zv - B) - AB * log1pf(B / zv);
+                Z = gl < gv ? zl : zv;
+            }
+        }
+    }
+    const float lzb = __logf(Z - B), L = log1pf(B / Z);
+    const float invB = 1.0f / B;
+    const float u = ((Z - 1.0f) + A * L * invB) * invB, v = 2.0f * L * invB;
+    bool ok = isfinite(u) && isfinite(v) && isfinite(lzb);
+#pragma unroll
+    for (int i = 0; i < NC; i++) lnphi[i] = fmaf(Bi[i], u, -lzb) - psi[i] * v;
+    return ok;
+}
+
+// ---------------------------------------------------------------------------
 // Rachford-Rice (Eq. RR) on the Leibovici-Neoschil window (Appendix C):
 // Newton on h = (theta - a_l)(a_r - theta) f_RR inside a shrinking bracket,
 // bisection when Newton leaves it; stops after a Newton step below 1e-8
@@ -684,6 +754,22 @@ __device__ __forceinline__ double dem_factor(const double* dk, const double* d1)
     const double lam = p01 / n1;
     if (!(lam > 0.0 && lam < 1.0)) return 0.0;
     return lam / (1.0 - lam);
+}
+
+// FP32 copy for the FP32 stability pre-iteration
+template <int NC>
+__device__ __forceinline__ float dem_factor_f(const float* dk, const float* d1) {
+    float n0 = 0.0f, n1 = 0.0f, p01 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        n0 = fmaf(dk[i], dk[i], n0);
+        n1 = fmaf(d1[i], d1[i], n1);
+        p01 = fmaf(dk[i], d1[i], p01);
+    }
+    if (!(n1 > 0.0f) || !(n0 < n1)) return 0.0f;
+    const float lam = p01 / n1;
+    if (!(lam > 0.0f && lam < 1.0f)) return 0.0f;
+    return lam / (1.0f - lam);
 }
 
 template <int NC>

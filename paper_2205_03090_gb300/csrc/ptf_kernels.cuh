@@ -57,7 +57,9 @@ enum { Q_STAB = 0, Q_SPLIT = 1, Q_STAB_TR = 2, Q_SPLIT_TR = 3, Q_SPLIT_TR_SLOW =
 // the longest runs start first and the kernel's tail shortens.  Only the
 // order of the work changes.
 constexpr double kSlowSS = 0.3;
-enum { H_PRE = 8, H_STAB = 9, H_STAB_TR = 10, H_SPLIT = 11, H_SPLIT_TR = 12, H_SPLIT_B = 13 };
+// ws.tflag bit: a stability item the FP32 pre-iteration handed to the FP64 SS
+constexpr int kSSFinish = 1 << 20;
+enum { H_PRE = 8, H_STAB = 9, H_STAB_TR = 10, H_SPLIT = 11, H_SPLIT_TR = 12, H_SPLIT_B = 13, H_STAB_FIN = 14 };
 
 // Component data of a launch.  OneSys: one fluid system, a kernel parameter
 // read through the constant bank.  ManySys: several systems of the same nc (a
@@ -415,6 +417,33 @@ struct StabSS {
         dem_pending = false;
     }
 
+    // Continue from the iterate the FP32 pre-iteration left (flag kSSFinish):
+    // the same evaluation count, so the cap counts both.  Returns false if the
+    // item is not waiting for FP64.
+    template <class CS>
+    __device__ __forceinline__ bool begin_finish(const CS& cs, const WS& ws, const IO& io, int64_t it_) {
+        const int64_t n = ws.n;
+        item = it_;
+        m = ws.q_stab[item >> 1];
+        t = (int)(item & 1);
+        const int32_t f = ws.tflag[t * n + m];
+        if (!(f & kSSFinish)) return false;
+        load_mix<NC>(ws, m, mx);
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            d[i] = ws.d[i * n + m];
+            lnW[i] = ws.lnW[(t * NC + i) * n + m];
+            dp[i] = 0.0;
+        }
+        res_prev = INFINITY;
+        dem_f = 0.0;
+        tm = 0.0;
+        iters = f & 0xff;
+        it = (f >> 8) & 0xff;
+        dem_pending = false;
+        return true;
+    }
+
     __device__ __forceinline__ void store(const WS& ws, int flags) {
         const int64_t n = ws.n;
 #pragma unroll
@@ -478,10 +507,131 @@ struct StabSS {
     }
 };
 
+// ---------------------------------------------------------------------------
+// FP32 pre-iteration of stability SS (mixed-precision refinement): the same
+// SS with DEM from the same start, evaluated by eos_f, until the update falls
+// below kSSFinishRes, or tm comes within kSSFinishTm of zero (FP32 rounding
+// of tm is about 1e-6), or the iteration cap.  The item then waits for the
+// FP64 iteration (kSSFinish), which evaluates the point again and takes every
+// decision: convergence, the first negative tm (so the run stops where an
+// FP64 run would), the cap.  At the cap the item goes to the trust region as
+// in the FP64 iteration.  FP32 operations cost a small fraction of an FP64 one
+// here; the FP64 iteration is left a third of the evaluations.
+// ---------------------------------------------------------------------------
+constexpr float kSSFinishRes = 3e-5f;
+constexpr float kSSFinishTm = 3e-6f;
+
+template <int NC>
+struct StabSS32 {
+    int64_t m, item;
+    int t, it, iters;
+    bool dem_pending;
+    float sA[NC], B[NC], d[NC], lnW[NC], dp[NC], dem_f, res_prev;
+
+    template <class CS>
+    __device__ __forceinline__ void begin(const CS& cs, const WS& ws, const IO& io, int64_t it_) {
+        const int64_t n = ws.n;
+        item = it_;
+        m = ws.q_stab[item >> 1];
+        const Comp<NC>& cp = cs.of(m);
+        t = (int)(item & 1);
+        double lnKw[NC];
+        if (io.status[m] & ST_NN_INIT) {
+#pragma unroll
+            for (int i = 0; i < NC; i++) lnKw[i] = ws.lnK[i * n + m];
+        } else {
+            wilson<NC>(cp, io.P[m], io.T[m], lnKw);
+        }
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            sA[i] = (float)ws.sA[i * n + m];
+            B[i] = (float)ws.B[i * n + m];
+            d[i] = (float)ws.d[i * n + m];
+            const double lz = ws.lnz[i * n + m];
+            lnW[i] = (float)(t == 0 ? lz + lnKw[i] : lz - lnKw[i]);
+            dp[i] = 0.0f;
+        }
+        res_prev = INFINITY;
+        dem_f = 0.0f;
+        it = iters = 0;
+        dem_pending = false;
+    }
+
+    // hand the current point on: to the FP64 iteration (finish) or the trust region
+    __device__ __forceinline__ void store(const WS& ws, int this_it, bool finish) {
+        const int64_t n = ws.n;
+#pragma unroll
+        for (int i = 0; i < NC; i++) ws.lnW[(t * NC + i) * n + m] = (double)lnW[i];
+        ws.tm[t * n + m] = 0.0;
+        ws.tflag[t * n + m] = finish ? (iters | (this_it << 8) | kSSFinish) : (iters | (1 << 16));
+    }
+
+    // 0 continue, 2 needs the trust region, 3 waits for the FP64 iteration
+    template <class CS>
+    __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io) {
+        const Comp<NC>& cp = cs.of(m);
+        float W[NC], c[NC], lnphi[NC], gt[NC], Wt = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            W[i] = __expf(lnW[i]);
+            Wt += W[i];
+        }
+        const float inv = 1.0f / Wt;
+#pragma unroll
+        for (int i = 0; i < NC; i++) c[i] = W[i] * inv;
+        bool ok = eos_f<NC>(cp, sA, B, c, lnphi);
+        float tm = 1.0f, res = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            gt[i] = lnW[i] + lnphi[i] - d[i];
+            tm = fmaf(W[i], gt[i] - 1.0f, tm);
+            res = fmaxf(res, fabsf(gt[i]));
+        }
+        ok = ok && isfinite(tm) && isfinite(res);
+        const int this_it = it++;
+        if (dem_pending && (!ok || !(res < res_prev))) {  // undo the accelerated update
+            dem_pending = false;
+#pragma unroll
+            for (int i = 0; i < NC; i++) lnW[i] -= dp[i] * dem_f;
+            return 0;
+        }
+        dem_pending = false;
+        if (!ok || res < kSSFinishRes || tm < kSSFinishTm) {
+            store(ws, this_it, true);
+            return 3;
+        }
+        if (this_it >= kSSStab) {
+            store(ws, this_it, false);
+            return 2;
+        }
+        float dk[NC];
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            dk[i] = -gt[i];
+            lnW[i] += dk[i];
+        }
+        const int s = iters + 1;
+        if (s % kDemPeriod == 0) {
+            const float f = dem_factor_f<NC>(dk, dp);
+            if (f > 0.0f) {
+#pragma unroll
+                for (int i = 0; i < NC; i++) lnW[i] += dk[i] * f;
+                dem_f = f;
+                dem_pending = true;
+                res_prev = res;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NC; i++) dp[i] = dk[i];
+        iters = s;
+        return 0;
+    }
+};
+
 template <int NC, class CS>
-__global__ void __launch_bounds__(128) k_stab_ss(const __grid_constant__ CS cs, WS ws, IO io) {
+__global__ void __launch_bounds__(128) k_stab_ss32(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = 2 * (int64_t)(*(volatile int32_t*)(ws.cnt + Q_STAB));
-    StabSS<NC> s;
+    StabSS32<NC> s;
     bool have = false, drained = false;
     for (;;) {
         const int64_t pos = warp_fetch(ws.cnt + H_STAB, !have, len, drained);
@@ -490,6 +640,23 @@ __global__ void __launch_bounds__(128) k_stab_ss(const __grid_constant__ CS cs, 
             have = true;
         }
         if (!__any_sync(0xffffffffu, have)) break;
+        const int r = have ? s.step(cs, ws, io) : 0;
+        warp_append(ws.cnt + Q_STAB_TR, ws.q_stab_tr, r == 2, (int32_t)s.item);
+        if (r) have = false;
+    }
+}
+
+// FP64 stability SS: finishes the items the FP32 pre-iteration handed on
+// (kSSFinish); the others are done or wait for the trust region.
+template <int NC, class CS>
+__global__ void __launch_bounds__(128) k_stab_ss(const __grid_constant__ CS cs, WS ws, IO io) {
+    const int64_t len = 2 * (int64_t)(*(volatile int32_t*)(ws.cnt + Q_STAB));
+    StabSS<NC> s;
+    bool have = false, drained = false;
+    for (;;) {
+        const int64_t pos = warp_fetch(ws.cnt + H_STAB_FIN, !have, len, drained);
+        if (pos >= 0) have = s.begin_finish(cs, ws, io, pos);
+        if (!__any_sync(0xffffffffu, have) && drained) break;
         const int r = have ? s.step(cs, ws, io) : 0;
         warp_append(ws.cnt + Q_STAB_TR, ws.q_stab_tr, r == 2, (int32_t)s.item);
         if (r) have = false;

@@ -54,6 +54,7 @@ cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, 
     const int sms = grid / 8 > 0 ? grid / 8 : 1;
     static const int g_pre = persistent_grid(k_precheck<NC, CS>, sms);
     static const int g_sss = persistent_grid(k_stab_ss<NC, CS>, sms);
+    static const int g_s32 = persistent_grid(k_stab_ss32<NC, CS>, sms);
     static const int g_sps = persistent_grid(k_split_ss<NC, CS>, sms);
     static const int g_str = persistent_grid(k_stab_tr<NC, CS>, sms);
     static const int g_spt = persistent_grid(k_split_tr<NC, CS>, sms);
@@ -89,6 +90,7 @@ cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, 
         k_split_ss<NC, CS><<<fg > 0 ? fg : 1, 128, 0, cc->lo>>>(cs, ws, io, 0, kFillerQuota);
         cudaEventRecord(cc->lo_done, cc->lo);
     }
+    k_stab_ss32<NC, CS><<<pg(g_s32), 128, 0, s>>>(cs, ws, io);
     k_stab_ss<NC, CS><<<pg(g_sss), 128, 0, s>>>(cs, ws, io);
     mark(2);
     k_stab_tr<NC, CS><<<pg(g_str), 128, 0, s>>>(cs, ws, io);
