@@ -27,7 +27,10 @@ constexpr double kOmegaB = 0.08664;   // Eq. b_i
 constexpr double kWilson = 5.373;     // Eq. wilson
 constexpr double kTolStab = 1e-6;     // Sec. 2.2.1, Appendix B.1
 constexpr double kTolSplitTR = 1e-8;  // Appendix B.2
-constexpr double kTolFug = 1e-10;     // fugacity residual of a converged split
+// Fugacity residual at which a split stops: 2 % below the 1e-10 target, so
+// that the target still holds when another FP64 implementation re-evaluates
+// the point (rounding moves the residual by ~1e-15).
+constexpr double kTolFug = 0.98e-10;
 constexpr int kSSStab = 9;            // Alg. 2
 constexpr int kTRStab = 20;           // Alg. 2
 constexpr int kSSSplit = 9;           // Sec. 2.2.2
@@ -531,6 +534,48 @@ __device__ __forceinline__ bool rachford_rice(const double* z, const double* K, 
     }
 #pragma unroll
     for (int i = 0; i < NC; i++) t[i] = 1.0 / fma(km1[i], th, 1.0);
+    theta = th;
+    return true;
+}
+
+// FP32 Rachford-Rice for the FP32 precheck evaluations: the same iteration
+// as rachford_rice in FP32 (stop at a step below 1e-6 relative).
+template <int NC>
+__device__ __forceinline__ bool rachford_rice_f(const float* z, const float* K, float& theta, float* t) {
+    float kmax = K[0], kmin = K[0];
+#pragma unroll
+    for (int i = 1; i < NC; i++) {
+        kmax = fmaxf(kmax, K[i]);
+        kmin = fminf(kmin, K[i]);
+    }
+    if (!(kmax > 1.0f && kmin < 1.0f)) return false;
+    const float al = 1.0f / (1.0f - kmax), ar = 1.0f / (1.0f - kmin);
+    float lo = al, hi = ar, th = theta;
+    if (!(th > lo && th < hi)) th = 0.5f * (fmaxf(lo, 0.0f) + fminf(hi, 1.0f));
+    float km1[NC];
+#pragma unroll
+    for (int i = 0; i < NC; i++) km1[i] = K[i] - 1.0f;
+#pragma unroll 1
+    for (int it = 0; it < 60; it++) {
+        float f = 0.0f, fp = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            const float a = __fdividef(km1[i], fmaf(km1[i], th, 1.0f));
+            f = fmaf(a, z[i], f);
+            fp = fmaf(-a * a, z[i], fp);
+        }
+        if (f > 0.0f) lo = th; else hi = th;
+        const float g1 = th - al, g2 = ar - th;
+        float tn = th - (g1 * g2 * f) / ((g2 - g1) * f + g1 * g2 * fp);
+        if (fabsf(tn - th) <= 1e-6f * fmaxf(1.0f, fabsf(th))) {
+            th = tn;
+            break;
+        }
+        th = (tn > lo && tn < hi) ? tn : 0.5f * (lo + hi);
+        if (!(lo < hi)) break;
+    }
+#pragma unroll
+    for (int i = 0; i < NC; i++) t[i] = 1.0f / fmaf(km1[i], th, 1.0f);
     theta = th;
     return true;
 }

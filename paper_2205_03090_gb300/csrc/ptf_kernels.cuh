@@ -59,7 +59,8 @@ enum { Q_STAB = 0, Q_SPLIT = 1, Q_STAB_TR = 2, Q_SPLIT_TR = 3, Q_SPLIT_TR_SLOW =
 constexpr double kSlowSS = 0.3;
 // ws.tflag bit: a stability item the FP32 pre-iteration handed to the FP64 SS
 constexpr int kSSFinish = 1 << 20;
-enum { H_PRE = 8, H_STAB = 9, H_STAB_TR = 10, H_SPLIT = 11, H_SPLIT_TR = 12, H_SPLIT_B = 13, H_STAB_FIN = 14 };
+enum { H_PRE = 8, H_STAB = 9, H_STAB_TR = 10, H_SPLIT = 11, H_SPLIT_TR = 12, H_SPLIT_B = 13, H_STAB_FIN = 14,
+       H_PRE32 = 15 };
 
 // Component data of a launch.  OneSys: one fluid system, a kernel parameter
 // read through the constant bank.  ManySys: several systems of the same nc (a
@@ -278,6 +279,22 @@ struct PrecheckSS {
         it = 0;
     }
 
+    // Continue after the FP32 evaluations (PrecheckSS32): ln K and theta from
+    // the workspace, the last evaluation to go.
+    template <class CS>
+    __device__ __forceinline__ void begin_finish(const CS& cs, const WS& ws, const IO& io, int64_t mm) {
+        const int64_t n = ws.n;
+        m = mm;
+        load_mix<NC>(ws, m, mx);
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            z[i] = io.z[i * io.ld + m];
+            lnK[i] = ws.lnK[i * n + m];
+        }
+        th = ws.theta[m];
+        it = kPrecheck - 1;
+    }
+
     // 0 continue, 1 to the stability queue, 2 to the split queue
     template <class CS>
     __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io) {
@@ -321,11 +338,92 @@ struct PrecheckSS {
     }
 };
 
-// Persistent kernel: lanes whose mixture finished take the next one, so the
-// warp keeps all lanes busy until the batch is exhausted.  Three resident
-// blocks per SM (168 registers, the rest spilled): the extra warps hide more
-// FP64 latency than the spills cost (also for split SS and split TR; the
-// stability TR kernel is no faster that way).
+// FP32 precheck evaluations (mixed-precision refinement, as the FP32
+// stability pre-iteration): all but the last of the kPrecheck evaluations
+// from Wilson K, by rachford_rice_f and eos_f.  theta outside (0, 1) or no
+// Rachford-Rice root sends the mixture to stability analysis as in the FP64
+// evaluation; otherwise ln K and theta wait in the workspace for the last,
+// FP64 evaluation and the tests, which k_precheck takes.  FP32 rounding can
+// only move mixtures whose theta lies within about 1e-6 of 0 or 1 between
+// the two routes, both of which end at the same result.
+template <int NC>
+struct PrecheckSS32 {
+    int64_t m;
+    float sA[NC], B[NC], z[NC], lnK[NC], th;
+    int it;
+
+    template <class CS>
+    __device__ __forceinline__ void begin(const CS& cs, const WS& ws, const IO& io, int64_t mm) {
+        const int64_t n = ws.n;
+        m = mm;
+        const Comp<NC>& cp = cs.of(m);
+        double lk[NC];
+        wilson<NC>(cp, io.P[m], io.T[m], lk);
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            sA[i] = (float)ws.sA[i * n + m];
+            B[i] = (float)ws.B[i * n + m];
+            z[i] = (float)io.z[i * io.ld + m];
+            lnK[i] = (float)lk[i];
+        }
+        th = 0.5f;
+        it = 0;
+    }
+
+    // 0 continue, 1 to the stability queue, 3 waits for the FP64 evaluation
+    template <class CS>
+    __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io) {
+        const Comp<NC>& cp = cs.of(m);
+        const int64_t n = ws.n;
+        float K[NC], t[NC], x[NC], y[NC], pl[NC], pv[NC];
+#pragma unroll
+        for (int i = 0; i < NC; i++) K[i] = __expf(lnK[i]);
+        if (!rachford_rice_f<NC>(z, K, th, t) || !(th > 0.0f && th < 1.0f)) {
+            io.status[m] = ST_STAB_RUN;
+            return 1;
+        }
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            x[i] = z[i] * t[i];
+            y[i] = K[i] * x[i];
+        }
+        const bool ok = eos_f<NC>(cp, sA, B, x, pl) && eos_f<NC>(cp, sA, B, y, pv);
+#pragma unroll
+        for (int i = 0; i < NC; i++) lnK[i] = pl[i] - pv[i];
+        if (!ok || ++it >= kPrecheck - 1) {  // hand on (a non-finite FP32 point is evaluated in FP64)
+#pragma unroll
+            for (int i = 0; i < NC; i++) ws.lnK[i * n + m] = ok ? (double)lnK[i] : 0.0;
+            ws.theta[m] = ok ? (double)th : 0.5;
+            return 3;
+        }
+        return 0;
+    }
+};
+
+template <int NC, class CS>
+__global__ void __launch_bounds__(128) k_precheck32(const __grid_constant__ CS cs, WS ws, IO io) {
+    const int64_t len = ws.n;
+    PrecheckSS32<NC> s;
+    bool have = false, drained = false;
+    for (;;) {
+        const int64_t pos = warp_fetch(ws.cnt + H_PRE32, !have, len, drained);
+        if (pos >= 0 && !(io.status[pos] & ST_NONFINITE)) {
+            s.begin(cs, ws, io, pos);
+            have = true;
+        }
+        if (!__any_sync(0xffffffffu, have) && drained) break;
+        const int r = have ? s.step(cs, ws, io) : 0;
+        warp_append(ws.cnt + Q_STAB, ws.q_stab, r == 1, (int32_t)s.m);
+        if (r) have = false;
+    }
+}
+
+// FP64 precheck: the last evaluation and the tests for the mixtures the FP32
+// evaluations handed on (status still 0).  Persistent kernel: lanes whose
+// mixture finished take the next one.  Three resident blocks per SM (168
+// registers, the rest spilled): the extra warps hide more FP64 latency than
+// the spills cost (also for split SS and split TR; the stability TR kernel is
+// no faster that way).
 template <int NC, class CS>
 __global__ void __launch_bounds__(128, 3) k_precheck(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = ws.n;
@@ -334,10 +432,10 @@ __global__ void __launch_bounds__(128, 3) k_precheck(const __grid_constant__ CS 
     for (;;) {
         const int64_t pos = warp_fetch(ws.cnt + H_PRE, !have, len, drained);
         if (pos >= 0) {
-            if (io.status[pos] & ST_NONFINITE) {
-                // already final; this lane fetches again next round
+            if (io.status[pos] != 0) {
+                // final, or sent to stability analysis already; this lane fetches again next round
             } else {
-                s.begin(cs, ws, io, pos);
+                s.begin_finish(cs, ws, io, pos);
                 have = true;
             }
         }

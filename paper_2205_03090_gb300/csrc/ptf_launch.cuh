@@ -53,6 +53,7 @@ cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, 
                             int pgrid = 0, const Conc* cc = nullptr) {
     const int sms = grid / 8 > 0 ? grid / 8 : 1;
     static const int g_pre = persistent_grid(k_precheck<NC, CS>, sms);
+    static const int g_p32 = persistent_grid(k_precheck32<NC, CS>, sms);
     static const int g_sss = persistent_grid(k_stab_ss<NC, CS>, sms);
     static const int g_s32 = persistent_grid(k_stab_ss32<NC, CS>, sms);
     static const int g_sps = persistent_grid(k_split_ss<NC, CS>, sms);
@@ -72,6 +73,7 @@ cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, 
     mark(0);
     if (mode == 0) {
         k_prep<NC, true, CS><<<grid, 128, 0, s>>>(cs, ws, io);
+        k_precheck32<NC, CS><<<pg(g_p32), 128, 0, s>>>(cs, ws, io);
         k_precheck<NC, CS><<<pg(g_pre), 128, 0, s>>>(cs, ws, io);
     } else if (mode == 2) {
         k_prep<NC, true, CS><<<grid, 128, 0, s>>>(cs, ws, io);
