@@ -60,7 +60,7 @@ constexpr double kSlowSS = 0.3;
 // ws.tflag bit: a stability item the FP32 pre-iteration handed to the FP64 SS
 constexpr int kSSFinish = 1 << 20;
 enum { H_PRE = 8, H_STAB = 9, H_STAB_TR = 10, H_SPLIT = 11, H_SPLIT_TR = 12, H_SPLIT_B = 13, H_STAB_FIN = 14,
-       H_PRE32 = 15 };
+       H_PRE32 = 15, H_SPLIT32 = 16, H_SPLIT32_B = 17 };
 
 // Component data of a launch.  OneSys: one fluid system, a kernel parameter
 // read through the constant bank.  ManySys: several systems of the same nc (a
@@ -998,7 +998,7 @@ struct SplitSS {
     Mix<NC> mx;
     double z[NC], lnK[NC], dp[NC], dem_f, res_prev, th;
     int it, iters;
-    bool dem_pending;
+    bool dem_pending, slow_hint;
 
     template <class CS>
     __device__ __forceinline__ void begin(const CS& cs, const WS& ws, const IO& io, int64_t mm) {
@@ -1012,11 +1012,26 @@ struct SplitSS {
             lnK[i] = ws.lnK[i * n + m];
             dp[i] = 0.0;
         }
+        slow_hint = false;
         th = 0.5;
         res_prev = INFINITY;
         dem_f = 0.0;
         it = iters = 0;
         dem_pending = false;
+    }
+
+    // Continue from the point the FP32 pre-iteration (SplitSS32) left: ln K,
+    // theta and the counts from the workspace; that point is evaluated again.
+    template <class CS>
+    __device__ __forceinline__ void begin_finish(const CS& cs, const WS& ws, const IO& io, int64_t mm) {
+        begin(cs, ws, io, mm);
+        th = ws.theta[m];
+        const int32_t f = ws.tflag[m];
+        iters = f & 0xff;
+        it = (f >> 8) & 0xff;
+        slow_hint = (f >> 16) & 1;
+#pragma unroll
+        for (int i = 0; i < NC; i++) dp[i] = ws.nV[i * ws.n + m];
     }
 
     __device__ __forceinline__ void finish(const IO& io, int32_t add_status) {
@@ -1089,7 +1104,8 @@ struct SplitSS {
             for (int i = 0; i < NC; i++)
                 ws.nV[i * n + m] = inside ? th * y[i] : 0.5 * K[i] * z[i] / (1.0 + 0.5 * (K[i] - 1.0));
             finish(io, ST_SPLIT_TR);
-            return res > kSlowSS * maxabs<NC>(dp) ? 3 : 2;
+            const double dpm = maxabs<NC>(dp);  // 0 when this iteration took no update yet
+            return (dpm > 0.0 ? res > kSlowSS * dpm : slow_hint) ? 3 : 2;
         }
         double dk[NC];
 #pragma unroll
@@ -1117,6 +1133,153 @@ struct SplitSS {
     }
 };
 
+// ---------------------------------------------------------------------------
+// FP32 pre-iteration of the phase-split SS (mixed-precision refinement, as
+// for stability analysis): the same SS with DEM from the same K, evaluated by
+// rachford_rice_f and eos_f, until the update falls below kSplitFinishRes or
+// the cap; then, and for every case that needs a decision (no Rachford-Rice
+// root, K near 1, a non-finite point), the FP64 iteration evaluates the point
+// again and continues: convergence to the fugacity residual, collapse, the
+// trust-region hand-off and every output are FP64.
+// ---------------------------------------------------------------------------
+constexpr float kSplitFinishRes = 3e-5f;
+
+template <int NC>
+struct SplitSS32 {
+    int64_t m;
+    float sA[NC], B[NC], z[NC], lnK[NC], dp[NC], dem_f, res_prev, th;
+    int it, iters;
+    bool dem_pending;
+
+    template <class CS>
+    __device__ __forceinline__ void begin(const CS& cs, const WS& ws, const IO& io, int64_t mm) {
+        const int64_t n = ws.n;
+        m = mm;
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            sA[i] = (float)ws.sA[i * n + m];
+            B[i] = (float)ws.B[i * n + m];
+            z[i] = (float)io.z[i * io.ld + m];
+            lnK[i] = (float)ws.lnK[i * n + m];
+            dp[i] = 0.0f;
+        }
+        th = 0.5f;
+        res_prev = INFINITY;
+        dem_f = 0.0f;
+        it = iters = 0;
+        dem_pending = false;
+    }
+
+    // hand the current point to the FP64 iteration, with the last update (in
+    // ws.nV, free until the trust-region hand-off; DEM continues from it) and
+    // the split TR queue order hint (kSlowSS) in case the FP64 iteration takes
+    // no update before the trust region
+    __device__ __forceinline__ int hand_on(const WS& ws, int this_it, bool slow) {
+        const int64_t n = ws.n;
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            ws.lnK[i * n + m] = (double)lnK[i];
+            ws.nV[i * n + m] = (double)dp[i];
+        }
+        ws.theta[m] = (double)th;
+        ws.tflag[m] = iters | (this_it << 8) | (slow ? 1 << 16 : 0);
+        return 3;
+    }
+
+    // 0 continue, 3 waits for the FP64 iteration
+    template <class CS>
+    __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io) {
+        const Comp<NC>& cp = cs.of(m);
+        float K[NC], t[NC], x[NC], y[NC], pl[NC], pv[NC], gt[NC];
+        float kmx = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            K[i] = __expf(lnK[i]);
+            kmx = fmaxf(kmx, fabsf(lnK[i]));
+        }
+        const int this_it = it++;
+        const float th0 = th;
+        bool ok = kmx > 1e-4f && rachford_rice_f<NC>(z, K, th, t);
+        float res = INFINITY;
+        if (ok) {
+#pragma unroll
+            for (int i = 0; i < NC; i++) {
+                x[i] = z[i] * t[i];
+                y[i] = K[i] * x[i];
+            }
+            ok = eos_f<NC>(cp, sA, B, x, pl) && eos_f<NC>(cp, sA, B, y, pv);
+            res = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NC; i++) {
+                gt[i] = lnK[i] + pv[i] - pl[i];
+                res = fmaxf(res, fabsf(gt[i]));
+            }
+            ok = ok && res < INFINITY;
+        }
+        if (dem_pending && (!ok || !(res < res_prev))) {  // undo the accelerated update
+            dem_pending = false;
+#pragma unroll
+            for (int i = 0; i < NC; i++) lnK[i] -= dp[i] * dem_f;
+            return 0;
+        }
+        dem_pending = false;
+        if (!ok) {
+            th = th0;
+            return hand_on(ws, this_it, false);
+        }
+        if (res < kSplitFinishRes || this_it >= kSSSplit) {
+            float dpm = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NC; i++) dpm = fmaxf(dpm, fabsf(dp[i]));
+            return hand_on(ws, this_it, res > (float)kSlowSS * dpm);
+        }
+        float dk[NC];
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            dk[i] = -gt[i];
+            lnK[i] += dk[i];
+        }
+        const int s = iters + 1;
+        if (s % kDemPeriod == 0) {
+            const float f = dem_factor_f<NC>(dk, dp);
+            if (f > 0.0f) {
+#pragma unroll
+                for (int i = 0; i < NC; i++) lnK[i] += dk[i] * f;
+                dem_f = f;
+                dem_pending = true;
+                res_prev = res;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NC; i++) dp[i] = dk[i];
+        iters = s;
+        return 0;
+    }
+};
+
+// part and quota as in k_split_ss
+template <int NC, class CS>
+__global__ void __launch_bounds__(128) k_split_ss32(const __grid_constant__ CS cs, WS ws, IO io, int part, int quota) {
+    const int64_t na = *(volatile int32_t*)(ws.cnt + Q_SPLIT), nb = *(volatile int32_t*)(ws.cnt + Q_SPLIT_B);
+    const int64_t len = part == 0 ? na : (part == 1 ? nb : na + nb);
+    const int64_t front = part == 1 ? 0 : na;
+    int32_t* head = ws.cnt + (part == 1 ? H_SPLIT32_B : H_SPLIT32);
+    __shared__ int blk_taken;
+    if (threadIdx.x == 0) blk_taken = 0;
+    __syncthreads();
+    SplitSS32<NC> s;
+    bool have = false, drained = false;
+    for (;;) {
+        const int64_t pos = warp_fetch(head, !have, len, drained, &blk_taken, quota);
+        if (pos >= 0) {
+            s.begin(cs, ws, io, ws.q_split[pos < front ? pos : ws.n - 1 - (pos - front)]);
+            have = true;
+        }
+        if (!__any_sync(0xffffffffu, have)) break;
+        if (have && s.step(cs, ws, io)) have = false;
+    }
+}
+
 // part 0: the front of the split queue; 1: its back; 2: both.  quota > 0:
 // each block takes at most about `quota` items and exits (short blocks, so
 // that a concurrent higher-priority kernel gets SMs as they free up);
@@ -1135,7 +1298,7 @@ __global__ void __launch_bounds__(128, 3) k_split_ss(const __grid_constant__ CS 
     for (;;) {
         const int64_t pos = warp_fetch(head, !have, len, drained, &blk_taken, quota);
         if (pos >= 0) {
-            s.begin(cs, ws, io, ws.q_split[pos < front ? pos : ws.n - 1 - (pos - front)]);
+            s.begin_finish(cs, ws, io, ws.q_split[pos < front ? pos : ws.n - 1 - (pos - front)]);
             have = true;
         }
         if (!__any_sync(0xffffffffu, have)) break;

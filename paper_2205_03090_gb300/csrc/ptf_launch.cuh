@@ -57,6 +57,7 @@ cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, 
     static const int g_sss = persistent_grid(k_stab_ss<NC, CS>, sms);
     static const int g_s32 = persistent_grid(k_stab_ss32<NC, CS>, sms);
     static const int g_sps = persistent_grid(k_split_ss<NC, CS>, sms);
+    static const int g_s3s = persistent_grid(k_split_ss32<NC, CS>, sms);
     static const int g_str = persistent_grid(k_stab_tr<NC, CS>, sms);
     static const int g_spt = persistent_grid(k_split_tr<NC, CS>, sms);
     auto pg = [&](int g) { return pgrid > 0 ? pgrid : g; };
@@ -89,6 +90,7 @@ cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, 
         cudaEventRecord(cc->pre, s);
         cudaStreamWaitEvent(cc->lo, cc->pre, 0);
         const int fg = (int)((ws.n + kFillerQuota - 1) / kFillerQuota);
+        k_split_ss32<NC, CS><<<fg > 0 ? fg : 1, 128, 0, cc->lo>>>(cs, ws, io, 0, kFillerQuota);
         k_split_ss<NC, CS><<<fg > 0 ? fg : 1, 128, 0, cc->lo>>>(cs, ws, io, 0, kFillerQuota);
         cudaEventRecord(cc->lo_done, cc->lo);
     }
@@ -101,6 +103,7 @@ cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, 
     else k_stab_out<NC, CS><<<grid, 128, 0, s>>>(cs, ws, io);
     mark(4);
     if (mode != 1) {
+        k_split_ss32<NC, CS><<<pg(g_s3s), 128, 0, s>>>(cs, ws, io, conc ? 1 : 2, 0);
         k_split_ss<NC, CS><<<pg(g_sps), 128, 0, s>>>(cs, ws, io, conc ? 1 : 2, 0);
         if (conc) cudaStreamWaitEvent(s, cc->lo_done, 0);
         mark(5);

@@ -99,16 +99,11 @@ def test_adjoint_vector_jacobian_products(ptf, oracle_mod):
     assert np.quantile(err, 0.999) < 1e-8 and err.max() < 1e-6
 
 
-def test_adjoint_matches_gpu_finite_differences(ptf):
-    """Central differences (relative step 1e-6) of the GPU flash itself, all
-    perturbed copies in one batch; the feed perturbation is renormalised."""
-    import torch
-    comp, cond, fl, P, T, z, res = _setup(ptf, 4000)
-    nc = comp.nc
-    nph = res.nphase.cpu().numpy()
-    st = res.status.cpu().numpy()
-    K = res.K.cpu().numpy()
-    idx = np.nonzero((nph == 2) & ((st & 16) == 0) & (np.abs(np.log(K)).max(axis=0) > 0.3))[0][:150]
+def _perturbed(cond, idx, nc, rel):
+    """Central-difference batch: for each of the nc + 2 inputs (P, T, z_k) of
+    the mixtures idx, a +h and a -h copy (relative step rel; the perturbed
+    feed is renormalised).  Returns P, T, z of 2 (nc + 2) m mixtures and the
+    steps h [nc + 2, m]."""
     m = len(idx)
     ncol = nc + 2
     Pn, Tn, zn = cond.P[idx], cond.T[idx], cond.z[:, idx]
@@ -119,41 +114,83 @@ def test_adjoint_matches_gpu_finite_differences(ptf):
     for c in range(ncol):
         for sgn, row in ((1, 2 * c), (-1, 2 * c + 1)):
             if c == 0:
-                h = 1e-6 * Pn
+                h = rel * Pn
                 Pb[row] = Pn + sgn * h
             elif c == 1:
-                h = 1e-6 * Tn
+                h = rel * Tn
                 Tb[row] = Tn + sgn * h
             else:
-                h = 1e-6 * zn[c - 2]
+                h = rel * zn[c - 2]
                 zz = zn.copy()
                 zz[c - 2] += sgn * h
                 zb[row] = zz / zz.sum(axis=0, keepdims=True)
             hs[c] = h
-    flat = lambda a: np.ascontiguousarray(a.reshape(a.shape[0] * a.shape[-1]) if a.ndim == 2 else a)
-    Pf, Tf = flat(Pb), flat(Tb)
+    Pf, Tf = Pb.reshape(-1), Tb.reshape(-1)
     zf = np.ascontiguousarray(zb.transpose(1, 0, 2).reshape(nc, -1))
-    d = [torch.tensor(a, device="cuda") for a in (Pf, Tf, zf)]
-    r = fl.ptflash_flash(d[0], d[1], d[2].contiguous())
-    torch.cuda.synchronize()
-    v = np.concatenate([r.beta.cpu().numpy()[None], r.x.cpu().numpy(), r.y.cpu().numpy()], 0)  # [1+2nc, 2 ncol m]
-    v = v.reshape(1 + 2 * nc, 2 * ncol, m)
-    both2 = (r.nphase.cpu().numpy().reshape(2 * ncol, m) == 2).all(axis=0)
+    return np.ascontiguousarray(Pf), np.ascontiguousarray(Tf), zf, hs
+
+
+def _central(beta, x, y, nph, hs, nc, m):
+    """Central differences [m, 1 + 2 nc, nc + 2] from the outputs of a
+    _perturbed batch, and the mixtures whose perturbed copies all stayed two-phase."""
+    ncol = nc + 2
+    v = np.concatenate([beta[None], x, y], 0).reshape(1 + 2 * nc, 2 * ncol, m)
+    both2 = (nph.reshape(2 * ncol, m) == 2).all(axis=0)
     fd = np.zeros((m, 1 + 2 * nc, ncol))
     for c in range(ncol):
         fd[:, :, c] = ((v[:, 2 * c] - v[:, 2 * c + 1]) / (2 * hs[c])).T
+    return fd, both2
+
+
+def _fd_setup(ptf):
+    comp, cond, fl, P, T, z, res = _setup(ptf, 4000)
+    nc = comp.nc
+    nph = res.nphase.cpu().numpy()
+    st = res.status.cpu().numpy()
+    K = res.K.cpu().numpy()
+    idx = np.nonzero((nph == 2) & ((st & 16) == 0) & (np.abs(np.log(K)).max(axis=0) > 0.3))[0][:150]
     Pg, Tg, zg = (t[idx].contiguous() if t.dim() == 1 else t[:, idx].contiguous() for t in (P, T, z))
     sub = ptf.FlashResult(*(None if t is None else (t[idx].contiguous() if t.dim() == 1 else t[:, idx].contiguous())
                             for t in (res.nphase, res.beta, res.x, res.y, res.K, res.status, res.iters)))
     J, ast = _gpu_jacobian_rows(fl, Pg, Tg, zg, sub, nc)
+    return comp, cond, fl, idx, J
+
+
+def test_adjoint_matches_oracle_finite_differences(ptf, oracle_mod):
+    """Central differences (relative step 1e-6) of the oracle's flash, whose
+    FP64 iteration path varies smoothly with the inputs, against the GPU
+    adjoint at the GPU's converged point."""
+    comp, cond, fl, idx, J = _fd_setup(ptf)
+    nc, m = comp.nc, len(idx)
+    Pf, Tf, zf, hs = _perturbed(cond, idx, nc, 1e-6)
+    s = oracle_mod.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
+    o = oracle_mod.flash(s, Pf, Tf, zf)
+    fd, both2 = _central(o["beta"], o["x"], o["y"], o["nphase"], hs, nc, m)
+    scale = np.maximum(np.abs(J).max(axis=1, keepdims=True), 1e-12)
+    err = (np.abs(fd - J) / scale).max(axis=(1, 2))[both2]
+    print("oracle FD vs GPU adjoint: median", np.median(err), "95%", np.quantile(err, 0.95), "max", err.max(),
+          "of", len(err))
+    assert len(err) > 100 and np.median(err) < 1e-6 and np.quantile(err, 0.95) < 1e-5 and err.max() < 1e-3
+
+
+def test_adjoint_matches_gpu_finite_differences(ptf):
+    """Central differences of the GPU flash itself, all perturbed copies in one
+    batch.  Its outputs are converged to the 1e-10 fugacity residual; below
+    that level they depend on where each run's FP32 and FP64 iterations stop,
+    so the step is 1e-4 relative (residual noise / step ~ 1e-6)."""
+    import torch
+    comp, cond, fl, idx, J = _fd_setup(ptf)
+    nc, m = comp.nc, len(idx)
+    Pf, Tf, zf, hs = _perturbed(cond, idx, nc, 1e-4)
+    d = [torch.tensor(a, device="cuda") for a in (Pf, Tf, zf)]
+    r = fl.ptflash_flash(d[0], d[1], d[2].contiguous())
+    torch.cuda.synchronize()
+    fd, both2 = _central(r.beta.cpu().numpy(), r.x.cpu().numpy(), r.y.cpu().numpy(), r.nphase.cpu().numpy(),
+                         hs, nc, m)
     scale = np.maximum(np.abs(J).max(axis=1, keepdims=True), 1e-12)
     err = (np.abs(fd - J) / scale).max(axis=(1, 2))[both2]
     print("GPU FD vs adjoint: median", np.median(err), "95%", np.quantile(err, 0.95), "max", err.max(), "of", len(err))
-    # The flash converges to a fugacity residual of 1e-10 (reading R10), so a
-    # relative step of 1e-6 leaves finite-difference noise up to ~1e-4
-    # relative, more where the split is ill-conditioned; the adjoint itself is
-    # pinned to 1e-8 against the oracle's Jacobian above.
-    assert len(err) > 100 and np.median(err) < 1e-6 and np.quantile(err, 0.95) < 1e-5 and err.max() < 1e-3
+    assert len(err) > 100 and np.median(err) < 1e-5 and np.quantile(err, 0.95) < 1e-3
 
 
 def test_autograd_function(ptf):
