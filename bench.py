@@ -47,10 +47,11 @@ LEARNED_DESC = ("10 SRK pseudo-components drawn as above, 1e7 mixtures, T~U(250,
 
 
 # DRAM bytes per unit of work of a kernel, from one ncu capture of
-# dram__bytes_read.sum + dram__bytes_write.sum (profiles/ncu_stab_ss_nc8_3e5.md:
-# k_stab_ss on 3e5 mixtures, 381,526 trial items, 143.4 MB); the bench scales
-# it by this run's units.  Only valid for the kernel as captured.
-TRAFFIC_PER_UNIT = {"stab_ss": (143.384e6 / 381526, "trial items", lambda q: 2 * q["stab"])}
+# dram__bytes_read.sum + dram__bytes_write.sum (profiles/ncu_split_tr_nc8_3e5.md:
+# k_split_tr on 3e5 mixtures, 70,597 split trust-region mixtures, 889.9 MB);
+# the bench scales it by this run's units.  Only valid for the kernel as
+# captured.
+TRAFFIC_PER_UNIT = {"split_tr": (889.898e6 / 70597, "split trust-region mixtures", lambda q: q["split_tr"])}
 
 
 def rank_conditions(w: dict, n: int, rank: int):
