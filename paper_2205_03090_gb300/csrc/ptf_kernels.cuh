@@ -6,14 +6,19 @@
 // sequence of launches on one stream with no host synchronisation.
 //
 //   prep_precheck : per-mixture constants, ln z, d = ln z + ln phi(z), Wilson
-//                   K, 3 split-SS iterations, tpd tests -> STAB or SPLIT queue
+//                   K, 3 split-SS iterations (two in FP32, the last and the
+//                   tpd tests in FP64) -> STAB or SPLIT queue
 //   stab_ss       : one item per (mixture, trial); SS with DEM (Eq.
-//                   ss_analyser) -> done or STAB_TR queue
+//                   ss_analyser), FP32 pre-iteration then FP64 -> done or
+//                   STAB_TR queue
 //   stab_tr       : trust region in beta = 2 sqrt(W) (Appendix B.1)
 //   stab_decide   : label, K re-estimate (Sec. 2.2.1) -> SPLIT queue or done
-//   split_ss      : SS with DEM and Rachford-Rice (Sec. 2.2.2) -> done or
-//                   SPLIT_TR queue
+//   split_ss      : SS with DEM and Rachford-Rice (Sec. 2.2.2), FP32
+//                   pre-iteration then FP64 -> done or SPLIT_TR queue
 //   split_tr      : trust region on G in n^V (Appendix B.2) + Newton polish
+//
+// The FP32 stages only move the point the FP64 iteration starts from; every
+// decision and every stored result is FP64.
 //
 // All arrays are SoA with the mixture index fastest ([i * n + m]), so a warp
 // of consecutive mixtures reads and writes coalesced 256-byte rows.
@@ -267,20 +272,8 @@ struct PrecheckSS {
     double z[NC], lnK[NC], th;
     int it;
 
-    template <class CS>
-    __device__ __forceinline__ void begin(const CS& cs, const WS& ws, const IO& io, int64_t mm) {
-        m = mm;
-        const Comp<NC>& cp = cs.of(m);
-        load_mix<NC>(ws, m, mx);
-#pragma unroll
-        for (int i = 0; i < NC; i++) z[i] = io.z[i * io.ld + m];
-        wilson<NC>(cp, io.P[m], io.T[m], lnK);
-        th = 0.5;
-        it = 0;
-    }
-
-    // Continue after the FP32 evaluations (PrecheckSS32): ln K and theta from
-    // the workspace, the last evaluation to go.
+    // Start after the FP32 evaluations (PrecheckSS32, which starts from Wilson
+    // K): ln K and theta from the workspace, the last evaluation to go.
     template <class CS>
     __device__ __forceinline__ void begin_finish(const CS& cs, const WS& ws, const IO& io, int64_t mm) {
         const int64_t n = ws.n;
@@ -486,38 +479,9 @@ struct StabSS {
     int t, it, iters;
     bool dem_pending;
 
-    template <class CS>
-    __device__ __forceinline__ void begin(const CS& cs, const WS& ws, const IO& io, int64_t it_) {
-        const int64_t n = ws.n;
-        item = it_;
-        m = ws.q_stab[item >> 1];
-        const Comp<NC>& cp = cs.of(m);
-        t = (int)(item & 1);
-        load_mix<NC>(ws, m, mx);
-        double lnKw[NC];
-        if (io.status[m] & ST_NN_INIT) {  // learned form: trials from the initializer's K (Sec. 4.3)
-#pragma unroll
-            for (int i = 0; i < NC; i++) lnKw[i] = ws.lnK[i * n + m];
-        } else {
-            wilson<NC>(cp, io.P[m], io.T[m], lnKw);
-        }
-#pragma unroll
-        for (int i = 0; i < NC; i++) {
-            d[i] = ws.d[i * n + m];
-            const double lz = ws.lnz[i * n + m];
-            lnW[i] = t == 0 ? lz + lnKw[i] : lz - lnKw[i];  // W = K z (vapour-like), z / K (liquid-like)
-            dp[i] = 0.0;
-        }
-        res_prev = INFINITY;
-        dem_f = 0.0;
-        tm = 0.0;
-        it = iters = 0;
-        dem_pending = false;
-    }
-
-    // Continue from the iterate the FP32 pre-iteration left (flag kSSFinish):
-    // the same evaluation count, so the cap counts both.  Returns false if the
-    // item is not waiting for FP64.
+    // Start from the iterate the FP32 pre-iteration (StabSS32, which starts
+    // from the trial K) left (flag kSSFinish): the same evaluation count, so
+    // the cap counts both.  Returns false if the item is not waiting for FP64.
     template <class CS>
     __device__ __forceinline__ bool begin_finish(const CS& cs, const WS& ws, const IO& io, int64_t it_) {
         const int64_t n = ws.n;
