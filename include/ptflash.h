@@ -19,7 +19,15 @@
  *    stream (cudaStream_t passed as void*, NULL = legacy default stream).
  *    They enqueue work and return without synchronising; results are valid
  *    once the stream has completed.  The context owns all scratch memory,
- *    so calls that share one context must be ordered on one stream.
+ *    so calls that share one context must be ordered on one stream.  A flash
+ *    without stage events (ptflash_set_profiling) forks onto two streams the
+ *    context owns (high and low priority) after the work already on `stream`
+ *    and joins them back into `stream`: ordering on `stream` is unchanged,
+ *    and the fork/join can be captured in a CUDA graph.
+ *  - Precision: every decision and every returned number is computed in
+ *    FP64.  FP32 runs the same iterations ahead of some FP64 ones (Rachford-
+ *    Rice and cubic seeds, the first precheck evaluations, the early SS
+ *    iterations); it only moves the point where the FP64 iteration starts.
  *  - Return value: 0 on success, a negative PTF_ERR_* code otherwise (no
  *    call aborts the process).  ptflash_strerror() names a code.
  *  - Per-mixture results carry a status bit set (PTF_ST_*).
