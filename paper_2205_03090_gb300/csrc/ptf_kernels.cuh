@@ -273,7 +273,9 @@ struct PrecheckSS {
     int it;
 
     // Start after the FP32 evaluations (PrecheckSS32, which starts from Wilson
-    // K): ln K and theta from the workspace, the last evaluation to go.
+    // K): ln K and theta from the workspace, the last evaluation to go.  A NaN
+    // theta marks an FP32 evaluation that was not finite: then all the
+    // evaluations run here, from Wilson K, as without the FP32 stage.
     template <class CS>
     __device__ __forceinline__ void begin_finish(const CS& cs, const WS& ws, const IO& io, int64_t mm) {
         const int64_t n = ws.n;
@@ -286,6 +288,11 @@ struct PrecheckSS {
         }
         th = ws.theta[m];
         it = kPrecheck - 1;
+        if (!(th == th)) {
+            wilson<NC>(cs.of(m), io.P[m], io.T[m], lnK);
+            th = 0.5;
+            it = 0;
+        }
     }
 
     // 0 continue, 1 to the stability queue, 2 to the split queue
@@ -383,10 +390,14 @@ struct PrecheckSS32 {
         const bool ok = eos_f<NC>(cp, sA, B, x, pl) && eos_f<NC>(cp, sA, B, y, pv);
 #pragma unroll
         for (int i = 0; i < NC; i++) lnK[i] = pl[i] - pv[i];
-        if (!ok || ++it >= kPrecheck - 1) {  // hand on (a non-finite FP32 point is evaluated in FP64)
+        if (!ok) {  // the FP64 stage redoes every evaluation from Wilson K
+            ws.theta[m] = NAN;
+            return 3;
+        }
+        if (++it >= kPrecheck - 1) {  // hand on to the last, FP64 evaluation
 #pragma unroll
-            for (int i = 0; i < NC; i++) ws.lnK[i * n + m] = ok ? (double)lnK[i] : 0.0;
-            ws.theta[m] = ok ? (double)th : 0.5;
+            for (int i = 0; i < NC; i++) ws.lnK[i * n + m] = (double)lnK[i];
+            ws.theta[m] = (double)th;
             return 3;
         }
         return 0;
