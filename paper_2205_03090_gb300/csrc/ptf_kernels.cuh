@@ -1117,7 +1117,7 @@ struct SplitSS {
 // again and continues: convergence to the fugacity residual, collapse, the
 // trust-region hand-off and every output are FP64.
 // ---------------------------------------------------------------------------
-constexpr float kSplitFinishRes = 3e-5f;
+constexpr float kSplitFinishRes = 1e-5f;
 
 template <int NC>
 struct SplitSS32 {
