@@ -203,6 +203,31 @@ def test_edge_cases(ptf, oracle_mod):
     fl.close()
 
 
+def test_tiny_pressures_take_the_fp64_path(ptf, oracle_mod):
+    """Pressures down to 1e-40 (in the unit of Pc) make the reduced EOS
+    parameters underflow in FP32: the FP32 stages hand such mixtures to FP64
+    (the precheck redoes every evaluation from Wilson K), and the results
+    still match the oracle."""
+    import torch
+    comp = wl.pseudo_components(4, 2)
+    fl = ptf.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=4096)
+    rng = np.random.default_rng(5)
+    n = 64
+    P = 10.0 ** rng.uniform(-40.0, -20.0, n)
+    T = rng.uniform(200.0, 600.0, n)
+    z = rng.dirichlet(np.ones(4), n).T.copy()
+    out = fl.ptflash_flash(torch.tensor(P, device="cuda"), torch.tensor(T, device="cuda"),
+                           torch.tensor(z, device="cuda"))
+    torch.cuda.synchronize()
+    nph, st = out.nphase.cpu().numpy(), out.status.cpu().numpy()
+    s = oracle_mod.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
+    o = oracle_mod.flash(s, P, T, z)
+    assert (st & 64).sum() == 0
+    np.testing.assert_array_equal(nph, o["nphase"])
+    assert np.isfinite(out.beta.cpu().numpy()).all()
+    fl.close()
+
+
 def test_host_entry_point_matches_device(ptf):
     import torch
     comp, cond = wl.workload("nc3_1e4", 3000)
