@@ -38,3 +38,38 @@ def test_strerror_without_gpu():
     assert lib.ptflash_create(None, 4, 10) == -1
     assert lib.ptflash_create(ctypes.byref(h), 17, 10) == -5
     assert lib.ptflash_destroy(None) == -1
+
+
+def test_batch_argument_checks_without_gpu():
+    """ptflash_batch_create validates every system's data on the host before
+    any CUDA call: nc outside 2..16, an asymmetric or nonzero-diagonal k_ij, a
+    non-positive critical constant, a negative mixture count."""
+    import numpy as np
+    from paper_2205_03090_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    P = ctypes.c_void_p
+    lib.ptflash_batch_create.argtypes = [P, ctypes.c_int, P, P, P, P, P, P]
+
+    def create(nc, n, Tc, Pc, om, kij):
+        h = ctypes.c_void_p()
+        arrs = [np.ascontiguousarray(a) for a in (nc, n, Tc, Pc, om, kij)]
+        rc = lib.ptflash_batch_create(ctypes.byref(h), len(nc), *[a.ctypes.data_as(P) for a in arrs])
+        return rc, h
+
+    nc = np.array([3], np.int32)
+    n = np.array([10], np.int64)
+    Tc, Pc, om = np.array([300.0, 400.0, 500.0]), np.array([4.0, 3.5, 3.0]), np.array([0.1, 0.2, 0.3])
+    kij = np.zeros((3, 3))
+    bad_k = kij.copy()
+    bad_k[0, 1] = 0.05  # asymmetric
+    diag_k = kij.copy()
+    diag_k[1, 1] = 0.01  # nonzero diagonal
+    assert create(np.array([1], np.int32), n, Tc[:1], Pc[:1], om[:1], kij[:1, :1])[0] == -5
+    assert create(np.array([17], np.int32), n, np.ones(17), np.ones(17), np.ones(17), np.zeros((17, 17)))[0] == -5
+    assert create(nc, n, Tc, Pc, om, bad_k)[0] == -1
+    assert create(nc, n, Tc, Pc, om, diag_k)[0] == -1
+    assert create(nc, n, Tc, np.array([4.0, -1.0, 3.0]), om, kij)[0] == -1
+    assert create(nc, np.array([-1], np.int64), Tc, Pc, om, kij)[0] == -1
+    h = ctypes.c_void_p()
+    assert lib.ptflash_batch_create(None, 1, None, None, None, None, None, None) == -1
+    assert lib.ptflash_batch_create(ctypes.byref(h), 0, None, None, None, None, None, None) == -1
