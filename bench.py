@@ -39,7 +39,7 @@ FP64_FMA_PER_CLK_PER_SM = 2  # GB300 FP64 units (recipe: 1.25 TFLOP/s at 2.07 GH
 TOL = 1e-8
 LIB_STAGES = ("prep_precheck", "stab_ss", "stab_tr", "stab_decide", "split_ss", "split_tr")
 ORACLE_STAGE = {"prep_precheck": 0, "stab_ss": 1, "stab_tr": 2, "split_ss": 3, "split_tr": 4}
-KERNELS_PER_STEP = 9  # 8 stage kernels (split SS in two parts) + the counter fold
+KERNELS_PER_STEP = 13  # prep, 2 precheck, 2 stability SS, stability TR, decide, 4 split SS (two parts, FP32 + FP64), split TR, counter fold
 LEARNED_WORKLOAD = "nc10_2phase_1e7"
 LEARNED_DESC = ("10 SRK pseudo-components drawn as above, 1e7 mixtures, T~U(250,450) K, P~U(2,15) MPa, "
                 "z~Dirichlet(1); classifier 3x64 SiLU and ln K initializer 3x128 SiLU (BF16/FP32), "
