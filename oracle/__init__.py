@@ -119,9 +119,11 @@ def flash(sysc: System, P, T, z, nthreads: int | None = None):
 
     Returns a dict of NumPy arrays: nphase, beta, x, y, K ([nc, n]), status,
     iters (packed: split SS | split TR << 8 | stab SS << 16 | stab TR << 24),
-    tm_min (NaN where stability analysis did not run) and flops: the
-    algorithmic FP64 work summed over the batch per stage (prep+precheck,
-    stability SS, stability TR, split SS, split TR)."""
+    tm_min (NaN where stability analysis did not run), ops: the algorithmic
+    FP64 work summed over the batch, [stage, kind] with stages (prep+precheck,
+    stability SS, stability TR, split SS, split TR) and kinds (flops: add and
+    multiply 1, fused multiply-add 2; divisions; square roots; exponentials;
+    logarithms), and flops = ops[:, 0]."""
     P = _f64(P)
     T = _f64(T)
     z = _f64(z)
@@ -130,13 +132,14 @@ def flash(sysc: System, P, T, z, nthreads: int | None = None):
     assert z.shape == (nc, n)
     out = dict(nphase=np.zeros(n, np.int32), beta=np.zeros(n), x=np.zeros((nc, n)), y=np.zeros((nc, n)),
                K=np.zeros((nc, n)), status=np.zeros(n, np.int32), iters=np.zeros(n, np.int32),
-               tm_min=np.zeros(n), flops=np.zeros(5))
+               tm_min=np.zeros(n), ops=np.zeros((5, 5)))
     rc = _lib_handle().oracle_flash_batch(*sysc._args(), n, _p(P), _p(T), _p(z), _pi(out["nphase"]),
                                           _p(out["beta"]), _p(out["x"]), _p(out["y"]), _p(out["K"]),
                                           _pi(out["status"]), _pi(out["iters"]), _p(out["tm_min"]),
-                                          _p(out["flops"]), nthreads or default_threads())
+                                          _p(out["ops"]), nthreads or default_threads())
     if rc:
         raise ValueError("oracle_flash_batch failed")
+    out["flops"] = out["ops"][:, 0].copy()
     return out
 
 

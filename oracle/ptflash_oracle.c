@@ -42,7 +42,13 @@
  *       steps keep 0 < n^V_i < z_i by a 0.99 fraction-to-boundary cut.
  *   R10 Split convergence tightened from the printed 1e-8 to the fugacity
  *       residual 1e-10; trust-region runs stop at the printed 1e-8 and then
- *       take plain Newton steps until the residual is <= 1e-10 (at least one).
+ *       take plain Newton steps until the residual is <= 1e-10 (at least one,
+ *       at most 10).  The paper caps the stability trust region at 20
+ *       iterations (Alg. 2) but gives no cap for the split one (its Table 4
+ *       run needed at most 13): a cap of 60 lets the slow split runs near
+ *       three-phase conditions converge (the slowest seen took 33 iterations
+ *       with the polish), where a cap of 20 left 13 of 2e5 8-component
+ *       mixtures unconverged.
  *   R11 Precheck: 3 SS evaluations from Wilson K; theta outside (0,1) or no
  *       Rachford-Rice root at any of them routes to stability; otherwise the
  *       tests use x, y of the 3rd evaluation and the split continues from
@@ -93,8 +99,8 @@
 #define KSS_STAB 9            /* Alg. 2 */
 #define KTR_STAB 20           /* Alg. 2 */
 #define KSS_SPLIT 9           /* Sec. 2.2.2 */
-#define KTR_SPLIT 20          /* R9/R10: same cap as the stability TR */
-#define KNEWTON_POLISH 5      /* R10 */
+#define KTR_SPLIT 60          /* R10: the paper gives no split TR cap */
+#define KNEWTON_POLISH 10     /* R10 */
 #define NPRECHECK 3           /* Sec. 2.2.3 */
 #define EPS_NEG 1e-10         /* R8 */
 #define TRIVIAL_LNK 1e-6      /* R13 */
@@ -102,34 +108,46 @@
 
 /* ------------------------------------------------------------------------ */
 /* Algorithmic FP64 work, counted per stage along the path each mixture      */
-/* takes.  Each primitive is charged the work of the method's own numerics   */
-/* (Halley roots, Newton Rachford-Rice, Cholesky trust-region steps), not of  */
-/* the oracle's slower bracketing: add, multiply = 1 flop, fused multiply-add */
-/* = 2, divide and square root = 8, exp and log = 20 (textbook Newton and     */
-/* polynomial costs).  Stages: 0 prep+precheck, 1 stability SS, 2 stability   */
-/* TR, 3 split SS, 4 split TR.                                               */
+/* takes.  Each primitive is charged the operations of the method's own      */
+/* numerics (Halley roots, Newton Rachford-Rice, Cholesky trust-region       */
+/* steps), not of the oracle's slower bracketing.  Kinds, counted apart:     */
+/* plain flops (add, multiply = 1, fused multiply-add = 2), divisions,        */
+/* square roots, exponentials, logarithms.  Stages: 0 prep+precheck,         */
+/* 1 stability SS, 2 stability TR, 3 split SS, 4 split TR.  This is test     */
+/* instrumentation: it does not change what the oracle computes.             */
 /* ------------------------------------------------------------------------ */
 #define NSTAGE 5
-static _Thread_local double g_flops[NSTAGE];
+#define NKIND 5 /* flops, divisions, square roots, exponentials, logarithms */
+typedef struct { double fl, dv, sq, ex, lg; } or_ops;
+static _Thread_local double g_ops[NSTAGE][NKIND];
 static _Thread_local int g_stage;
-#define FLOPS(x) (g_flops[g_stage] += (double)(x))
-#define W_DIV 8.0
-#define W_EXP 20.0
-#define W_LOG 20.0
-/* per-primitive costs */
-static double cost_eos(int nc, int three) {
-    double c = 2.0 * nc * nc + 8.0 * nc     /* mixing sums */
-               + 18.0 + 2 * W_DIV           /* root count: 2 cubic evaluations, sqrt */
-               + 2 * (16.0 + W_DIV)         /* two FP64 Halley steps */
-               + 2 * (W_LOG + W_DIV)        /* ln(Z - B), ln(1 + B/Z) */
-               + 2 * W_DIV + 4.0 + 3.0 * nc;/* ln phi */
-    if (three) c += 10.0 + 2 * W_DIV + 2 * (8.0 + W_DIV) + 2 * (W_LOG + W_DIV) + 8.0; /* deflation, polish, gbar */
+static void count(or_ops o) {
+    g_ops[g_stage][0] += o.fl;
+    g_ops[g_stage][1] += o.dv;
+    g_ops[g_stage][2] += o.sq;
+    g_ops[g_stage][3] += o.ex;
+    g_ops[g_stage][4] += o.lg;
+}
+static or_ops ops(double fl, double dv, double sq, double ex, double lg) {
+    or_ops o = {fl, dv, sq, ex, lg};
+    return o;
+}
+static or_ops add_ops(or_ops a, or_ops b) { return ops(a.fl + b.fl, a.dv + b.dv, a.sq + b.sq, a.ex + b.ex, a.lg + b.lg); }
+static or_ops scale_ops(or_ops a, double k) { return ops(k * a.fl, k * a.dv, k * a.sq, k * a.ex, k * a.lg); }
+/* per-primitive counts */
+static or_ops cost_eos(int nc, int three) {
+    or_ops c = ops(2.0 * nc * nc + 8.0 * nc, 0, 0, 0, 0);   /* mixing sums */
+    c = add_ops(c, ops(18.0, 0, 1, 0, 0));                  /* root count: 2 cubic evaluations, sqrt */
+    c = add_ops(c, ops(2 * 16.0, 2, 0, 0, 0));              /* two FP64 Halley steps */
+    c = add_ops(c, ops(3.0, 1, 0, 0, 2));                   /* ln(Z - B), ln(1 + B/Z) */
+    c = add_ops(c, ops(4.0 + 3.0 * nc, 2, 0, 0, 0));        /* ln phi */
+    if (three) c = add_ops(c, ops(10.0 + 2 * 8.0 + 8.0, 1 + 2 + 2, 1, 0, 4)); /* deflation, polish, gbar */
     return c;
 }
-static double cost_jac(int nc) { return 7.0 * nc * (nc + 1) + 30.0 * nc + 8 * W_DIV; }
-static double cost_rr(int nc) { return 4.0 * (nc * (W_DIV + 6.0) + 10.0 + W_DIV) + nc * W_DIV; }
-static double cost_chol(int nc) { return 2.0 * nc * nc * nc / 6.0 + nc * (2 * W_DIV) + 2.0 * nc * nc; }
-static double cost_trsub(int nc) { return 3.0 * cost_chol(nc) + 4.0 * nc * nc; }
+static or_ops cost_jac(int nc) { return ops(7.0 * nc * (nc + 1) + 30.0 * nc, 8, 0, 0, 0); }
+static or_ops cost_rr(int nc) { return ops(4.0 * (6.0 * nc + 10.0), 4.0 * (nc + 1) + nc, 0, 0, 0); }
+static or_ops cost_chol(int nc) { return ops(2.0 * nc * nc * nc / 6.0 + 2.0 * nc * nc, nc, nc, 0, 0); }
+static or_ops cost_trsub(int nc) { return add_ops(scale_ops(cost_chol(nc), 3.0), ops(4.0 * nc * nc, 0, 0, 0, 0)); }
 
 /* ------------------------------------------------------------------------ */
 /* Component system and per-mixture EOS constants (Appendix A)              */
@@ -268,7 +286,7 @@ int or_eos(const or_mix* m, const double* c, or_phase* ph) {
     if (!have) return -1;
     double Z = zv;
     if (zl < zv && gbar(zl, A, B) < gbar(zv, A, B)) Z = zl;
-    FLOPS(cost_eos(nc, zl < zv));
+    count(cost_eos(nc, zl < zv));
     ph->A = A;
     ph->B = B;
     ph->Z = Z;
@@ -289,7 +307,7 @@ int or_eos(const or_mix* m, const double* c, or_phase* ph) {
 /* ------------------------------------------------------------------------ */
 void or_dlnphi_dn(const or_mix* m, const double* c, const or_phase* ph, double* J) {
     int nc = m->nc;
-    FLOPS(cost_jac(nc));
+    count(cost_jac(nc));
     double A = ph->A, B = ph->B, Z = ph->Z;
     double L = log(1.0 + B / Z);
     double FZ = 3.0 * Z * Z - 2.0 * Z + A - B - B * B;
@@ -334,7 +352,7 @@ int or_rr(int nc, const double* z, const double* K, double* theta) {
     double kmax = K[0], kmin = K[0];
     for (int i = 1; i < nc; i++) { if (K[i] > kmax) kmax = K[i]; if (K[i] < kmin) kmin = K[i]; }
     if (!(kmax > 1.0 && kmin < 1.0)) return -1;
-    FLOPS(cost_rr(nc));
+    count(cost_rr(nc));
     double lo = 1.0 / (1.0 - kmax), hi = 1.0 / (1.0 - kmin); /* alpha_l < 0 < 1 < alpha_r */
     for (int it = 0; it < 2000; it++) {
         double mid = 0.5 * (lo + hi);
@@ -408,7 +426,7 @@ static double unorm(int n, const double* gt, const double* lam, double eta) {
 }
 
 double or_tr_subproblem(int n, const double* H, const double* g, const double* mdiag, double radius, double* d) {
-    FLOPS(cost_trsub(n));
+    count(cost_trsub(n));
     double Hs[OR_MAXNC * OR_MAXNC], gs[OR_MAXNC], sc[OR_MAXNC];
     for (int i = 0; i < n; i++) sc[i] = mdiag ? 1.0 / sqrt(mdiag[i]) : 1.0;
     for (int i = 0; i < n; i++) {
@@ -468,7 +486,7 @@ double or_tr_subproblem(int n, const double* H, const double* g, const double* m
 /* Newton step -H^{-1} g through the eigendecomposition; returns 0 if H is
  * positive definite, -1 otherwise (no step). */
 static int newton_step(int n, const double* H, const double* g, double* d) {
-    FLOPS(cost_chol(n) + 2.0 * n * n);
+    count(add_ops(cost_chol(n), ops(2.0 * n * n, 0, 0, 0, 0)));
     double lam[OR_MAXNC], V[OR_MAXNC * OR_MAXNC];
     jacobi_eig(n, H, lam, V);
     for (int k = 0; k < n; k++) if (!(lam[k] > 0.0)) return -1;
@@ -520,7 +538,7 @@ typedef struct {
 /* tm (reading R2) and grad-tm/dW = ln W + ln phi(W) - d at a trial lnW. */
 static int stab_eval(const or_mix* m, const double* d, const double* lnW, or_phase* ph, double* gt, double* tm) {
     int nc = m->nc;
-    FLOPS(nc * W_EXP + W_DIV + 6.0 * nc);
+    count(ops(6.0 * nc, 1, 0, nc, 0));
     double W[OR_MAXNC], Wt = 0.0, c[OR_MAXNC];
     for (int i = 0; i < nc; i++) { W[i] = exp(lnW[i]); Wt += W[i]; }
     for (int i = 0; i < nc; i++) c[i] = W[i] / Wt;
@@ -553,7 +571,7 @@ static int stab_point(const or_mix* m, const double* d, const double* lnW, doubl
     for (int i = 0; i < nc; i++) { W[i] = exp(lnW[i]); Wt += W[i]; }
     for (int i = 0; i < nc; i++) c[i] = W[i] / Wt;
     or_dlnphi_dn(m, c, &ph, J);
-    FLOPS(nc * W_DIV + 4.0 * nc * (nc + 1) + 2 * nc);
+    count(ops(4.0 * nc * (nc + 1) + 2 * nc, 0, nc, 0, 0));
     for (int i = 0; i < nc; i++) g[i] = sqrt(W[i]) * gt[i];
     for (int i = 0; i < nc; i++)
         for (int j = 0; j < nc; j++)
@@ -626,7 +644,7 @@ void or_stability_trial(const or_mix* m, const double* d, or_trial* tr, int stop
             double b = fabs(beta[i] + step[i]); /* tm(beta) is even in each beta_i */
             lnWn[i] = 2.0 * log(0.5 * b);
         }
-        FLOPS(nc * (W_LOG + 3.0) + 2.0 * nc * nc);
+        count(ops(3.0 * nc + 2.0 * nc * nc, 0, 0, 0, nc));
         int bad = stab_point(m, d, lnWn, gtn, &tmn, gn, Hn);
         /* R9: below PRED_TRUST the predicted change is under the rounding
          * of tm itself and the ratio is noise: accept, keep the radius.
@@ -698,7 +716,7 @@ typedef struct {
 
 static int split_eval(const or_mix* m, const double* z, const double* nV, or_splitpt* s) {
     int nc = m->nc;
-    FLOPS(2 * W_DIV + 4.0 * nc + 2.0 * nc * W_LOG + 8.0 * nc + nc * (2 * W_DIV) + 5.0 * nc * (nc + 1) + 2.0 * nc * nc);
+    count(ops(12.0 * nc + 5.0 * nc * (nc + 1) + 2.0 * nc * nc, 2 + nc, nc, 0, 2.0 * nc));
     double th = 0.0;
     for (int i = 0; i < nc; i++) th += nV[i];
     s->th = th;
@@ -770,7 +788,7 @@ static void or_split(const or_mix* m, const double* z, double* lnK, or_result* r
         if (maxabs(nc, lnK) < TRIVIAL_LNK) fail = 1;
         if (!fail) {
             for (int i = 0; i < nc; i++) K[i] = exp(lnK[i]);
-            FLOPS(nc * W_EXP + 6.0 * nc);
+            count(ops(6.0 * nc, 0, 0, nc, 0));
             if (or_rr(nc, z, K, &th)) fail = 1;
         }
         if (!fail) {
@@ -892,7 +910,7 @@ void or_flash_one(const or_sys* s, double P, double T, const double* z, or_resul
     g_stage = 0;
     or_mix m;
     or_mix_init(s, P, T, &m);
-    FLOPS(nc * (2 * W_DIV + 12.0) + nc * W_LOG + nc * 4.0); /* constants, ln z, Wilson */
+    count(ops(16.0 * nc, nc, nc, 0, nc)); /* constants, ln z, Wilson */
     memset(r, 0, sizeof(*r));
     r->tm_min = NAN;
     double lnz[OR_MAXNC], d[OR_MAXNC], lnKw[OR_MAXNC], lnK[OR_MAXNC];
@@ -909,7 +927,7 @@ void or_flash_one(const or_sys* s, double P, double T, const double* z, or_resul
         or_phase pl, pv;
         for (int it = 0; it < NPRECHECK; it++) {
             for (int i = 0; i < nc; i++) K[i] = exp(lnK[i]);
-            FLOPS(nc * W_EXP + 6.0 * nc);
+            count(ops(6.0 * nc, 0, 0, nc, 0));
             if (or_rr(nc, z, K, &th) || !(th > 0.0 && th < 1.0)) { route_stab = 1; break; }
             xy_from(nc, z, K, th, x, y);
             if (or_eos(&m, x, &pl) || or_eos(&m, y, &pv)) { route_stab = 1; break; }
@@ -918,7 +936,7 @@ void or_flash_one(const or_sys* s, double P, double T, const double* z, or_resul
         if (!route_stab) {
             /* Eq. tpd on the current phases; Delta G by reading R3 */
             double tx = 0.0, ty = 0.0;
-            FLOPS(2.0 * nc * (W_LOG + 4.0) + 5.0);
+            count(ops(8.0 * nc + 5.0, 0, 0, 0, 2.0 * nc));
             for (int i = 0; i < nc; i++) {
                 tx += x[i] * (log(x[i]) + pl.lnphi[i] - d[i]);
                 ty += y[i] * (log(y[i]) + pv.lnphi[i] - d[i]);
@@ -996,14 +1014,14 @@ static void sys_from(int nc, const double* Tc, const double* Pc, const double* o
 int oracle_flash_batch(int nc, const double* Tc, const double* Pc, const double* om, const double* kij,
                        int64_t n, const double* P, const double* T, const double* z,
                        int32_t* nphase, double* beta, double* x, double* y, double* K,
-                       int32_t* status, int32_t* iters, double* tm_min, double* flops, int nthreads) {
+                       int32_t* status, int32_t* iters, double* tm_min, double* opcount, int nthreads) {
     if (nc < 2 || nc > OR_MAXNC) return -1;
     or_sys s;
     sys_from(nc, Tc, Pc, om, kij, &s);
-    double tot[NSTAGE] = {0};
+    double tot[NSTAGE][NKIND] = {{0}};
 #pragma omp parallel num_threads(nthreads)
     {
-    for (int q = 0; q < NSTAGE; q++) g_flops[q] = 0.0;
+    memset(g_ops, 0, sizeof(g_ops));
 #pragma omp for schedule(dynamic, 16)
     for (int64_t k = 0; k < n; k++) {
         double zz[OR_MAXNC];
@@ -1022,10 +1040,12 @@ int oracle_flash_batch(int nc, const double* Tc, const double* Pc, const double*
         if (tm_min) tm_min[k] = r.tm_min;
     }
 #pragma omp critical
-    for (int q = 0; q < NSTAGE; q++) tot[q] += g_flops[q];
+    for (int q = 0; q < NSTAGE; q++)
+        for (int k = 0; k < NKIND; k++) tot[q][k] += g_ops[q][k];
     }
-    if (flops)
-        for (int q = 0; q < NSTAGE; q++) flops[q] = tot[q];
+    if (opcount)
+        for (int q = 0; q < NSTAGE; q++)
+            for (int k = 0; k < NKIND; k++) opcount[q * NKIND + k] = tot[q][k];
     return 0;
 }
 
