@@ -36,6 +36,7 @@ WORKLOAD_DESC = ("8 SRK pseudo-components (Tc~U(150,650) K sorted, Pc~U(2,5) MPa
                  "k_ij~U(0,0.1)), 1e6 mixtures, T~U(200,600) K, P~U(0.1,20) MPa, z~Dirichlet(0.5)")
 SMS = 152
 FP64_FMA_PER_CLK_PER_SM = 2  # GB300 FP64 units (recipe: 1.25 TFLOP/s at 2.07 GHz)
+OP_KINDS = ("div", "sqrt", "exp", "log")  # counted apart from the plain flops by the oracle
 TOL = 1e-8
 LIB_STAGES = ("prep_precheck", "stab_ss", "stab_tr", "stab_decide", "split_ss", "split_tr")
 ORACLE_STAGE = {"prep_precheck": 0, "stab_ss": 1, "stab_tr": 2, "split_ss": 3, "split_tr": 4}
@@ -52,6 +53,16 @@ LEARNED_DESC = ("10 SRK pseudo-components drawn as above, 1e7 mixtures, T~U(250,
 # the bench scales it by this run's units.  Only valid for the kernel as
 # captured.
 TRAFFIC_PER_UNIT = {"split_tr": (889.898e6 / 70597, "split trust-region mixtures", lambda q: q["split_tr"])}
+
+
+def measured_hbm_gbs():
+    """The measured HBM copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json),
+    else the recipe's 6.8 TB/s fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
 
 
 def rank_conditions(w: dict, n: int, rank: int):
@@ -475,6 +486,8 @@ def ours_arm(args, ws, rank, local):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    # FP64 FMA probe of this GPU right after the timed steps (same clock record)
+    probe_tf, probe_ms = ptflash.fp64_fma_rate(6000)
     clk = clocks.stop()
     # Stage times: further steps with the library's per-stage events, which
     # run the stages one after another (in the timed steps the split SS of the
@@ -537,19 +550,23 @@ def ours_arm(args, ws, rank, local):
         import oracle as _or
         cores = _or.default_threads()
         frac = match_fraction(s, comp, cond, idx, o, g)
-        flops_per_flash = o["flops"] / sample  # by oracle stage
+        ops_per_flash = o["ops"] / sample  # [oracle stage, kind]
     else:
-        cpu_dt, cores, frac, flops_per_flash = float("nan"), 0, float("nan"), np.full(5, np.nan)
+        cpu_dt, cores, frac, ops_per_flash = float("nan"), 0, float("nan"), np.full((5, 5), np.nan)
 
     mean_stage = {k: float(np.mean([d[k] for d in stage_ms])) for k in LIB_STAGES}
     dom = max(mean_stage, key=mean_stage.get)
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
     peak = SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     if dom in ORACLE_STAGE:
-        work = flops_per_flash[ORACLE_STAGE[dom]] * n
+        q = ORACLE_STAGE[dom]
+        work = float(ops_per_flash[q, 0] * n)  # plain FP64 flops: add, multiply 1, FMA 2
+        special = {k: float(ops_per_flash[q, 1 + j] * n) for j, k in enumerate(OP_KINDS)}
         achieved = work / (mean_stage[dom] / 1e3) / 1e12
     else:
-        work, achieved = None, None
+        work, special, achieved = None, None, None
+    step_ops = {k: float(ops_per_flash[:, j].sum() * n) for j, k in enumerate(("flops",) + OP_KINDS)}
+    hbm_peak = measured_hbm_gbs()
     traffic, traffic_src = None, None
     if dom in TRAFFIC_PER_UNIT:
         per, unit, count = TRAFFIC_PER_UNIT[dom]
@@ -567,8 +584,19 @@ def ours_arm(args, ws, rank, local):
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "traffic_source": traffic_src,
-                     "peak_source": f"152 SMs x 2 FP64 FMA/clk x 2 flop x {sm_mhz:.0f} MHz (sampled median)",
-                     "work_per_launch_flop": work},
+                     "peak_source": f"152 SMs x 2 FP64 FMA/clk x 2 flop x {sm_mhz:.0f} MHz (sampled median); "
+                                    f"the FP64 FMA probe (ptflash_fp64_fma_rate) measured {probe_tf:.3f} TFLOP/s "
+                                    f"on this GPU after the timed steps",
+                     "peak_probe": probe_tf, "frac_of_probe": (achieved / probe_tf) if achieved else None,
+                     "fp64_ops": work, "transcendental_ops": special,
+                     "ops_note": "oracle-counted algorithmic work of the dominant stage per launch: fp64_ops are "
+                                 "plain flops (add, multiply 1, FMA 2); divisions, square roots, exponentials and "
+                                 "logarithms are counted apart (each costs many FP64 pipe slots on the GPU)",
+                     "step_ops": step_ops,
+                     "hbm_algorithmic_bytes_per_step": h2d + d2h,
+                     "hbm_achieved_gbs": (h2d + d2h) / (ms / 1e3) / 1e9,
+                     "hbm_peak_gbs": hbm_peak,
+                     "hbm_frac": ((h2d + d2h) / (ms / 1e3) / 1e9 / hbm_peak) if hbm_peak else None},
         "stage_ms": mean_stage,
         "stage_ms_note": "separate steps after the timed ones, stages one after another with per-stage CUDA events; "
                          "the timed steps overlap the precheck-routed split SS with the stability stages",

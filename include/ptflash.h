@@ -68,12 +68,32 @@ extern "C" {
 
 typedef struct ptflash_ctx ptflash_ctx;
 
-/* Options of one flash call (NULL = defaults). */
+/*
+ * Options of one flash call (NULL = defaults; ptflash_default_options fills
+ * the struct).  A zero cap or tolerance selects its default.  Caps must lie
+ * in [1, 200] and tolerances be positive and finite, else the call returns
+ * PTF_ERR_INVALID_ARG.  A run that reaches a cap without converging gets the
+ * PTF_ST_MAXITER status bit (its outputs are the point where it stopped).
+ */
 typedef struct {
-    int32_t use_nn;      /* 0 plain method (default); 1 classifier + initializer (Sec. 4.3) */
-    double p_l, p_r;     /* classifier thresholds (defaults 0.02, 0.98; Sec. 5.2) */
-    int32_t reserved[8];
+    int32_t use_nn;       /* 0 plain method (default); 1 classifier + initializer (Sec. 4.3) */
+    double p_l, p_r;      /* classifier thresholds (defaults 0.02, 0.98; Sec. 5.2) */
+    int32_t max_ss_stab;  /* SS evaluations per stability trial (default 9: K_ss of Alg. 2) */
+    int32_t max_tr_stab;  /* trust-region iterations per stability trial (default 20: K_tr of Alg. 2) */
+    int32_t max_ss_split; /* SS evaluations of the phase split (default 9: Sec. 2.2.2) */
+    int32_t max_tr_split; /* split trust-region iterations (default 60; the paper gives none) */
+    int32_t max_polish;   /* Newton steps after a split trust-region run (default 10) */
+    double tol_stab;      /* stability stop: max |d tm / d W_i| (default 1e-6: Sec. 2.2.1, Appendix B.1) */
+    double tol_split_tr;  /* split trust region hands on to the Newton polish below this fugacity
+                             residual (default 1e-8: Appendix B.2) */
+    double tol_fug;       /* split convergence: max_i |ln y_i + ln phi_i^V - ln x_i - ln phi_i^L|
+                             (default 0.98e-10: 2 % below the 1e-10 target, so that the target
+                             holds when another FP64 implementation re-evaluates the point) */
+    int32_t reserved[4];
 } ptflash_options;
+
+/* Fill *opt with the defaults (plain method).  PTF_ERR_INVALID_ARG if NULL. */
+int ptflash_default_options(ptflash_options* opt);
 
 /*
  * Create a context on the current CUDA device with device scratch for up to
@@ -317,6 +337,30 @@ int ptflash_nn_eval(ptflash_ctx* ctx, int which, int64_t n, const float* X, cons
  * memory and synchronises the device.
  */
 int ptflash_check_math(int64_t n, double* max_ulp_log, double* max_ulp_exp);
+
+/*
+ * Phase EOS at given compositions, the primitive every stage evaluates
+ * (Appendix A: Eqs. a_i, b_i and mixing_rule for A and B, the cubic of Eq.
+ * cubic_Z, the admissible root Z > B with the lower residual Gibbs energy
+ * gbar(Z) = Z - 1 - ln(Z - B) - (A/B) ln(1 + B/Z), and ln phi_i of Eq. lnphi).
+ * DEVICE arrays: P[n], T[n], composition c[nc * n] (component-major, mole
+ * fractions; not renormalised); outputs Z[n] and lnphi[nc * n].  Same
+ * context, stream and ownership rules as ptflash_flash.  Non-positive or
+ * non-finite inputs give non-finite outputs.
+ */
+int ptflash_phase_eos(ptflash_ctx* ctx, int64_t n, const double* P, const double* T, const double* c, double* Z,
+                      double* lnphi, void* stream);
+
+/*
+ * FP64 throughput probe of the current device (the peak against which the
+ * flash kernels' FP64 rate is read): one launch of 4 blocks of 256 threads per
+ * SM, each thread running 8 independent chains of `iters` x 4 fused
+ * multiply-adds, timed with CUDA events after a warm-up launch.  *tflops gets
+ * the rate (2 flops per FMA), *ms the launch time.  Synchronises the device.
+ * PTF_ERR_INVALID_ARG for iters outside [1, 2^32] or NULL outputs.  The paper
+ * has no counterpart: this measures the hardware the flash runs on.
+ */
+int ptflash_fp64_fma_rate(int64_t iters, double* tflops, double* ms);
 
 /* Human-readable name of an error code. */
 const char* ptflash_strerror(int code);

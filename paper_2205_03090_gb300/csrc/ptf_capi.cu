@@ -76,7 +76,75 @@ __global__ void k_check_math(int64_t n, unsigned long long* err) {
     }
 }
 
+// FP64 throughput probe: 8 independent FMA chains per thread, so that the
+// FP64 pipes (not the chain latency) bound the rate.  The final test can never
+// hold for these inputs; it keeps the chains live.
+__global__ void __launch_bounds__(256) k_fp64_fma(int64_t iters, double b, double cst, double* sink) {
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) a[k] = 1.0 + 1e-3 * threadIdx.x + k;
+#pragma unroll 1
+    for (int64_t i = 0; i < iters; i++) {
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int k = 0; k < 8; k++) a[k] = fma(a[k], b, cst);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) t += a[k];
+    if (t == -1.0) sink[0] = t;
+}
+
 extern "C" {
+
+int ptflash_fp64_fma_rate(int64_t iters, double* tflops, double* ms) {
+    if (iters < 1 || iters > ((int64_t)1 << 32) || !tflops || !ms) return PTF_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    PTF_CUDA(cudaGetDevice(&dev));
+    PTF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 4, threads = 256;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PTF_CUDA(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    float t = 0.0f;
+    if (e == cudaSuccess) {
+        k_fp64_fma<<<blocks, threads>>>(iters / 8 + 1, 0.999999999, 1e-9, nullptr);  // warm-up
+        e = cudaEventRecord(e0);
+    }
+    if (e == cudaSuccess) {
+        k_fp64_fma<<<blocks, threads>>>(iters, 0.999999999, 1e-9, nullptr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *ms = t;
+    *tflops = 2.0 * 32.0 * (double)iters * blocks * threads / (t * 1e-3) / 1e12;
+    return PTF_OK;
+}
+
+int ptflash_phase_eos(ptflash_ctx* c, int64_t n, const double* P, const double* T, const double* comp, double* Z,
+                      double* lnphi, void* stream) {
+    if (!c) return PTF_ERR_INVALID_ARG;
+    if (!c->have_comp) return PTF_ERR_NOT_READY;
+    if (n < 0) return PTF_ERR_INVALID_ARG;
+    if (n == 0) return PTF_OK;
+    if (!P || !T || !comp || !Z || !lnphi) return PTF_ERR_INVALID_ARG;
+    const int grid = c->sm_count * 8;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (c->comp.nc) {
+#define PTF_CASE(NC) \
+    case NC: PTF_CUDA(launch_eos<NC>(c->comp, n, P, T, comp, Z, lnphi, grid, s)); return PTF_OK;
+        PTF_CASE(2) PTF_CASE(3) PTF_CASE(4) PTF_CASE(5) PTF_CASE(6) PTF_CASE(7) PTF_CASE(8) PTF_CASE(9)
+        PTF_CASE(10) PTF_CASE(11) PTF_CASE(12) PTF_CASE(13) PTF_CASE(14) PTF_CASE(15) PTF_CASE(16)
+#undef PTF_CASE
+    }
+    return PTF_ERR_UNSUPPORTED;
+}
 
 int ptflash_check_math(int64_t n, double* max_ulp_log, double* max_ulp_exp) {
     if (n < 1 || n > (int64_t)1 << 28 || !max_ulp_log || !max_ulp_exp) return PTF_ERR_INVALID_ARG;
@@ -197,9 +265,47 @@ int ptflash_set_components(ptflash_ctx* c, int nc, const double* Tc, const doubl
     return PTF_OK;
 }
 
+// The options of one call: learned-form thresholds, tolerances and caps.
+struct CallOpts {
+    int mode = 0;  // 0 plain, 2 learned form
+    float p_l = 0.02f, p_r = 0.98f;
+    Ctl ctl;
+};
+
+// Validate *opt (NULL = defaults) into o.  The learned form needs both networks.
+static int parse_options(const ptflash_ctx* c, const ptflash_options* opt, CallOpts& o) {
+    o = CallOpts();
+    if (!opt) return PTF_OK;
+    auto cap = [](int32_t v, int& dst) {
+        if (v == 0) return true;
+        if (v < 1 || v > 200) return false;
+        dst = v;
+        return true;
+    };
+    auto tol = [](double v, double& dst) {
+        if (v == 0.0) return true;
+        if (!(v > 0.0) || !std::isfinite(v)) return false;
+        dst = v;
+        return true;
+    };
+    if (!cap(opt->max_ss_stab, o.ctl.ss_stab) || !cap(opt->max_tr_stab, o.ctl.tr_stab) ||
+        !cap(opt->max_ss_split, o.ctl.ss_split) || !cap(opt->max_tr_split, o.ctl.tr_split) ||
+        !cap(opt->max_polish, o.ctl.polish) || !tol(opt->tol_stab, o.ctl.tol_stab) ||
+        !tol(opt->tol_split_tr, o.ctl.tol_split_tr) || !tol(opt->tol_fug, o.ctl.tol_fug))
+        return PTF_ERR_INVALID_ARG;
+    if (opt->use_nn) {
+        if (!(opt->p_l >= 0.0 && opt->p_l <= opt->p_r && opt->p_r <= 1.0)) return PTF_ERR_INVALID_ARG;
+        if (!c->nn[0].ready || !c->nn[1].ready) return PTF_ERR_NOT_READY;
+        o.mode = 2;
+        o.p_l = (float)opt->p_l;
+        o.p_r = (float)opt->p_r;
+    }
+    return PTF_OK;
+}
+
 static int run(ptflash_ctx* c, int64_t n, const double* P, const double* T, const double* z, int32_t* o_i,
                double* o_d, double* x, double* y, double* K, int32_t* status, int32_t* iters, int mode,
-               bool zero_counts, cudaStream_t s, float p_l = 0.02f, float p_r = 0.98f) {
+               bool zero_counts, cudaStream_t s, float p_l = 0.02f, float p_r = 0.98f, const Ctl& ctl = Ctl()) {
     if (zero_counts) {
         PTF_CUDA(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
         for (int k = 0; k < kStages; k++) c->stage_ms[k] = 0.0;
@@ -207,6 +313,7 @@ static int run(ptflash_ctx* c, int64_t n, const double* P, const double* T, cons
     for (int64_t m0 = 0; m0 < n; m0 += c->n_max) {
         const int64_t cn = (n - m0 < c->n_max) ? n - m0 : c->n_max;
         WS ws = make_ws(c, cn);
+        ws.ctl = ctl;
         IO io;
         io.ld = n;
         io.P = P + m0;
@@ -243,16 +350,27 @@ int ptflash_flash(ptflash_ctx* c, int64_t n, const double* P, const double* T, c
     if (n < 0) return PTF_ERR_INVALID_ARG;
     if (n == 0) return PTF_OK;
     if (!P || !T || !z || !nphase || !beta || !x || !y || !K || !status) return PTF_ERR_INVALID_ARG;
-    int mode = 0;
-    float p_l = 0.02f, p_r = 0.98f;
-    if (opt && opt->use_nn) {
-        if (!c->nn[0].ready || !c->nn[1].ready) return PTF_ERR_NOT_READY;
-        if (!(opt->p_l >= 0.0 && opt->p_l <= opt->p_r && opt->p_r <= 1.0)) return PTF_ERR_INVALID_ARG;
-        mode = 2;
-        p_l = (float)opt->p_l;
-        p_r = (float)opt->p_r;
-    }
-    return run(c, n, P, T, z, nphase, beta, x, y, K, status, iters, mode, true, (cudaStream_t)stream, p_l, p_r);
+    CallOpts o;
+    if (int rc = parse_options(c, opt, o)) return rc;
+    return run(c, n, P, T, z, nphase, beta, x, y, K, status, iters, o.mode, true, (cudaStream_t)stream, o.p_l,
+               o.p_r, o.ctl);
+}
+
+int ptflash_default_options(ptflash_options* opt) {
+    if (!opt) return PTF_ERR_INVALID_ARG;
+    std::memset(opt, 0, sizeof(*opt));
+    const Ctl d;
+    opt->p_l = 0.02;
+    opt->p_r = 0.98;
+    opt->max_ss_stab = d.ss_stab;
+    opt->max_tr_stab = d.tr_stab;
+    opt->max_ss_split = d.ss_split;
+    opt->max_tr_split = d.tr_split;
+    opt->max_polish = d.polish;
+    opt->tol_stab = d.tol_stab;
+    opt->tol_split_tr = d.tol_split_tr;
+    opt->tol_fug = d.tol_fug;
+    return PTF_OK;
 }
 
 int ptflash_flash_adjoint(ptflash_ctx* c, int64_t n, const double* P, const double* T, const double* z,
@@ -307,15 +425,8 @@ int ptflash_flash_host(ptflash_ctx* c, int64_t n, const double* P, const double*
             return PTF_ERR_NO_MEMORY;
         }
     }
-    int mode = 0;
-    float p_l = 0.02f, p_r = 0.98f;
-    if (opt && opt->use_nn) {
-        if (!c->nn[0].ready || !c->nn[1].ready) return PTF_ERR_NOT_READY;
-        if (!(opt->p_l >= 0.0 && opt->p_l <= opt->p_r && opt->p_r <= 1.0)) return PTF_ERR_INVALID_ARG;
-        mode = 2;
-        p_l = (float)opt->p_l;
-        p_r = (float)opt->p_r;
-    }
+    CallOpts o;
+    if (int rc = parse_options(c, opt, o)) return rc;
     PTF_CUDA(cudaMemsetAsync(c->acc, 0, 8 * sizeof(unsigned long long), s));
     for (int64_t m0 = 0; m0 < n; m0 += nm) {
         const int64_t cn = (n - m0 < nm) ? n - m0 : nm;
@@ -333,7 +444,8 @@ int ptflash_flash_host(ptflash_ctx* c, int64_t n, const double* P, const double*
         PTF_CUDA(cudaMemcpyAsync(dP, P + m0, rowb, cudaMemcpyHostToDevice, s));
         PTF_CUDA(cudaMemcpyAsync(dT, T + m0, rowb, cudaMemcpyHostToDevice, s));
         PTF_CUDA(cudaMemcpy2DAsync(dz, rowb, z + m0, pitch, rowb, nc, cudaMemcpyHostToDevice, s));
-        int rc = run(c, cn, dP, dT, dz, dnp, dbeta, dx, dy, dK, dst, iters ? dit : nullptr, mode, false, s, p_l, p_r);
+        int rc = run(c, cn, dP, dT, dz, dnp, dbeta, dx, dy, dK, dst, iters ? dit : nullptr, o.mode, false, s, o.p_l,
+                     o.p_r, o.ctl);
         if (rc) return rc;
         PTF_CUDA(cudaMemcpyAsync(nphase + m0, dnp, cn * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         PTF_CUDA(cudaMemcpyAsync(status + m0, dst, cn * sizeof(int32_t), cudaMemcpyDeviceToHost, s));

@@ -34,12 +34,23 @@ constexpr double kTolFug = 0.98e-10;
 constexpr int kSSStab = 9;            // Alg. 2
 constexpr int kTRStab = 20;           // Alg. 2
 constexpr int kSSSplit = 9;           // Sec. 2.2.2
-constexpr int kTRSplit = 20;          // same cap as the stability TR
-constexpr int kNewtonPolish = 5;      // Newton steps after a split TR run
+// The paper gives no cap for the split trust region (its Table 4 run needed
+// at most 13 iterations); 60 lets the slow runs near three-phase conditions
+// converge (the slowest seen needed 33 iterations with the polish).
+constexpr int kTRSplit = 60;
+constexpr int kNewtonPolish = 10;     // Newton steps after a split TR run
 constexpr int kPrecheck = 3;          // Sec. 2.2.3
 constexpr double kEpsNeg = 1e-10;     // "negative" tm / tpd / Delta G
 constexpr double kTrivialLnK = 1e-6;  // split collapsed to K = 1
 constexpr double kPredTrust = 1e-12;  // ratio test trusted above this
+
+// Tolerances and iteration caps of one call (ptflash_options; the defaults
+// above).  Part of the workspace descriptor, a kernel parameter, so every
+// read is a uniform constant-bank load.
+struct Ctl {
+    int ss_stab = kSSStab, tr_stab = kTRStab, ss_split = kSSSplit, tr_split = kTRSplit, polish = kNewtonPolish;
+    double tol_stab = kTolStab, tol_split_tr = kTolSplitTR, tol_fug = kTolFug;
+};
 
 // status bits (same values as documented in include/ptflash.h)
 constexpr int ST_PRECHECK_UNSTABLE = 1;
@@ -172,10 +183,24 @@ __device__ __forceinline__ void wilson(const Comp<NC>& cp, double P, double T, d
 // far below what the paper's 1e-8 step criterion (Appendix A) guarantees.
 // With three real roots, deflation (Appendix A) gives the other two.  Among
 // admissible roots the smallest and the largest are compared by the residual
-// Gibbs energy gbar(Z) = Z - 1 - ln(Z - B) - (A/B) ln(1 + B/Z): in FP32 when
-// the two differ by more than 1e-4 (FP32 rounding is below 1e-5 here), else
-// in FP64 after one FP64 Newton polish of both.  The chosen root gets that
-// polish and its FP64 logarithms.
+// Gibbs energy gbar(Z) = Z - 1 - ln(Z - B) - (A/B) ln(1 + B/Z).  The chosen
+// root gets one FP64 Newton polish and its FP64 logarithms.
+//
+// Two decisions may be taken in FP32, each only where a bound on its FP32
+// rounding error proves that FP64 takes the same one (u = 2^-24):
+//  - the root count, from the signs of f at its critical points zm, zp (they
+//    exist for r1 < 1/3).  Horner's rule on z < 1 from r1, r0 rounded to
+//    FP32 is off by at most about 3u (z^3 + z^2 + |r1| z + r0) < 3u (3 + r0);
+//    zm and zp are off by O(u / sqrt(4 - 12 r1)), which moves f only at second
+//    order (f' vanishes there), so FP32 decides where 4 - 12 r1 > 1e-5 and
+//    both |f| exceed 1e-5 (1 + r0), some 25 times the bound;
+//  - the root choice, from the sign of gbar(zl) - gbar(zv).  zl - zv, zl - B,
+//    zv - B, B/zl and B/zv are formed in FP64 (so no cancellation happens in
+//    FP32) and rounded once; logf and log1pf then err by at most about one
+//    FP32 ulp of their results, so each of the five terms t_k of the
+//    difference is off by at most about 4u |t_k| + u, and FP32 decides where
+//    the difference exceeds 1e-5 (1 + sum |t_k|), some 40 times the bound.
+// Everywhere else both decisions are FP64.
 // ---------------------------------------------------------------------------
 struct Root {
     double Z, lzb, L;  // chosen root, ln(Z - B), ln(1 + B/Z)
@@ -191,9 +216,7 @@ __device__ __forceinline__ double cub_polish(double Z, double r1, double r0) {
 __device__ __forceinline__ Root cubic_select(double A, double B) {
     const double r1 = A - B * (1.0 + B), r0 = A * B;
     // real-root count from the critical points of f (local max zm, local min
-    // zp).  They exist only for r1 < 1/3, where every term of f at them is
-    // below 2 in size: FP32 decides when both values are clear of zero by
-    // 1e-5 (FP32 rounding is below 1e-6 there), FP64 otherwise.
+    // zp), in FP32 where the error bound above allows, else in FP64
     bool three = false;
     const float r1f = (float)r1, r0f = (float)r0;
     const float dcf = fmaf(-12.0f, r1f, 4.0f);
@@ -204,7 +227,8 @@ __device__ __forceinline__ Root cubic_select(double A, double B) {
             const float zmf = (2.0f - sqf) * (1.0f / 6.0f), zpf = (2.0f + sqf) * (1.0f / 6.0f);
             const float fm = fmaf(fmaf(zmf - 1.0f, zmf, r1f), zmf, -r0f);
             const float fpv = fmaf(fmaf(zpf - 1.0f, zpf, r1f), zpf, -r0f);
-            if (fabsf(fm) > 1e-5f && fabsf(fpv) > 1e-5f) {
+            const float tau = 1e-5f * (1.0f + fabsf(r0f));
+            if (fabsf(fm) > tau && fabsf(fpv) > tau) {
                 three = fm > 0.0f && fpv < 0.0f;
                 decided = true;
             }
@@ -267,10 +291,13 @@ __device__ __forceinline__ Root cubic_select(double A, double B) {
         double zl = fmin(z0, fmin(q1, q2)), zv = fmax(z0, fmax(q1, q2));
         bool low = false;
         if (zl > B && zl < zv) {
-            const float Bf = (float)B, ABf = (float)(A / B), zlf = (float)zl, zvf = (float)zv;
-            const float dg = (zlf - zvf) - (logf(zlf - Bf) - logf(zvf - Bf)) -
-                             ABf * (logf(1.0f + Bf / zlf) - logf(1.0f + Bf / zvf));
-            if (fabsf(dg) > 1e-4f) {
+            // FP32 sign of gbar(zl) - gbar(zv) with its error bound (above)
+            const float ABf = (float)(A / B);
+            const float t1 = (float)(zl - zv), t2 = logf((float)(zl - B)), t3 = logf((float)(zv - B));
+            const float t4 = ABf * log1pf((float)(B / zl)), t5 = ABf * log1pf((float)(B / zv));
+            const float dg = t1 - (t2 - t3) - (t4 - t5);
+            const float tau = 1e-5f * (1.0f + fabsf(t1) + fabsf(t2) + fabsf(t3) + fabsf(t4) + fabsf(t5));
+            if (fabsf(dg) > tau) {
                 low = dg < 0.0f;
             } else {
                 zl = cub_polish(zl, r1, r0);

@@ -37,6 +37,7 @@ struct WS {
     int32_t* cnt;      // queue counters and read heads (enums below)
     float* nnp = nullptr;  // learned form: classifier logits [n]
     float* nnk = nullptr;  // learned form: initializer ln K [NC n]
+    Ctl ctl;               // tolerances and iteration caps of the call
 };
 
 struct IO {
@@ -264,13 +265,44 @@ __global__ void __launch_bounds__(128) k_prep(const __grid_constant__ CS cs, WS 
 // ---------------------------------------------------------------------------
 // precheck (Sec. 2.2.3): three split-SS evaluations from Wilson K, then the
 // tpd(x), tpd(y), Delta G tests.  One step = one evaluation of one mixture.
+//
+// The first two evaluations run in FP32 (PrecheckSS32).  Their iterate differs
+// from an all-FP64 run's by about 1e-6 in ln K, so every route decision taken
+// on it carries a margin that bounds that difference with room to spare (a
+// relative 1e-4); a mixture whose decision falls inside the margin redoes all
+// three evaluations in FP64 from Wilson K.  The routes are therefore those of
+// an all-FP64 precheck.
+//
+// Rachford-Rice route: the root lies in (0, 1) iff f(0) = sum z_i (K_i - 1) > 0
+// and f(1) = sum z_i (1 - 1/K_i) < 0 (f decreases on its window, Appendix C);
+// otherwise (theta outside (0, 1), or K not bracketing 1) the mixture goes to
+// stability analysis.  Returns +1 root in (0, 1), -1 stability analysis, 0
+// within the relative margin `rel` of either sign test.
 // ---------------------------------------------------------------------------
+template <int NC, class F>
+__device__ __forceinline__ int rr_route(const F* z, const F* K, F rel) {
+    F f0 = 0, f1 = 0, s0 = 0, s1 = 0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        const F ik = F(1) / K[i];
+        f0 += z[i] * (K[i] - F(1));
+        f1 += z[i] * (F(1) - ik);
+        s0 += z[i] * K[i];
+        s1 += z[i] * ik;
+    }
+    if (f0 < -rel * s0 || f1 > rel * s1) return -1;
+    if (f0 > rel * s0 && f1 < -rel * s1) return 1;
+    return 0;
+}
+constexpr float kRouteMargin = 1e-4f;
+
 template <int NC>
 struct PrecheckSS {
     int64_t m;
     Mix<NC> mx;
     double z[NC], lnK[NC], th;
     int it;
+    bool from32;  // started from the FP32 evaluations
 
     // Start after the FP32 evaluations (PrecheckSS32, which starts from Wilson
     // K): ln K and theta from the workspace, the last evaluation to go.  A NaN
@@ -288,11 +320,17 @@ struct PrecheckSS {
         }
         th = ws.theta[m];
         it = kPrecheck - 1;
-        if (!(th == th)) {
-            wilson<NC>(cs.of(m), io.P[m], io.T[m], lnK);
-            th = 0.5;
-            it = 0;
-        }
+        from32 = true;
+        if (!(th == th)) restart(cs, io);
+    }
+
+    // all evaluations in FP64 from Wilson K
+    template <class CS>
+    __device__ __forceinline__ void restart(const CS& cs, const IO& io) {
+        wilson<NC>(cs.of(m), io.P[m], io.T[m], lnK);
+        th = 0.5;
+        it = 0;
+        from32 = false;
     }
 
     // 0 continue, 1 to the stability queue, 2 to the split queue
@@ -304,6 +342,10 @@ struct PrecheckSS {
         Phase<NC> pl, pv;
 #pragma unroll
         for (int i = 0; i < NC; i++) K[i] = exp_fast(lnK[i]);
+        if (from32 && rr_route<NC, double>(z, K, kRouteMargin) == 0) {  // too close to call on this iterate
+            restart(cs, io);
+            return 0;
+        }
         if (!rachford_rice<NC>(z, K, th, t) || !(th > 0.0 && th < 1.0)) {
             io.status[m] = ST_STAB_RUN;
             return 1;
@@ -318,15 +360,31 @@ struct PrecheckSS {
 #pragma unroll
         for (int i = 0; i < NC; i++) lnK[i] -= lnK[i] + pv.lnphi[i] - pl.lnphi[i];
         if (++it < kPrecheck) return 0;
-        // Eq. tpd for the current phases; Delta G = (1-theta) tpd(x) + theta tpd(y)
-        double tx = 0.0, ty = 0.0;
+        // Eq. tpd for the current phases; Delta G = (1-theta) tpd(x) + theta tpd(y).
+        // sx, sy: sum c_i |ln c_i + ln phi_i(c) - d_i|, the first-order size of a
+        // change of tpd per relative change of the phase compositions
+        double tx = 0.0, ty = 0.0, sx = 0.0, sy = 0.0;
 #pragma unroll
         for (int i = 0; i < NC; i++) {
             const double d = ws.d[i * n + m];
-            tx = fma(x[i], log_fast(x[i]) + pl.lnphi[i] - d, tx);
-            ty = fma(y[i], log_fast(y[i]) + pv.lnphi[i] - d, ty);
+            const double gx = log_fast(x[i]) + pl.lnphi[i] - d, gy = log_fast(y[i]) + pv.lnphi[i] - d;
+            tx = fma(x[i], gx, tx);
+            ty = fma(y[i], gy, ty);
+            sx = fma(x[i], fabs(gx), sx);
+            sy = fma(y[i], fabs(gy), sy);
         }
         const double dG = (1.0 - th) * tx + th * ty;
+        if (from32) {
+            // the tests on an FP32-started iterate must hold with a margin
+            const double mx_ = kRouteMargin * (1e-6 + sx), my_ = kRouteMargin * (1e-6 + sy);
+            const double mg = (1.0 - th) * mx_ + th * my_;
+            const bool neg = tx < -kEpsNeg - mx_ || ty < -kEpsNeg - my_ || dG < -kEpsNeg - mg;
+            const bool pos = tx > -kEpsNeg + mx_ && ty > -kEpsNeg + my_ && dG > -kEpsNeg + mg;
+            if (!neg && !pos) {
+                restart(cs, io);
+                return 0;
+            }
+        }
         if (!(tx < -kEpsNeg || ty < -kEpsNeg || dG < -kEpsNeg)) {
             io.status[m] = ST_STAB_RUN;
             return 1;
@@ -340,12 +398,12 @@ struct PrecheckSS {
 
 // FP32 precheck evaluations (mixed-precision refinement, as the FP32
 // stability pre-iteration): all but the last of the kPrecheck evaluations
-// from Wilson K, by rachford_rice_f and eos_f.  theta outside (0, 1) or no
-// Rachford-Rice root sends the mixture to stability analysis as in the FP64
-// evaluation; otherwise ln K and theta wait in the workspace for the last,
-// FP64 evaluation and the tests, which k_precheck takes.  FP32 rounding can
-// only move mixtures whose theta lies within about 1e-6 of 0 or 1 between
-// the two routes, both of which end at the same result.
+// from Wilson K, by rachford_rice_f and eos_f.  A Rachford-Rice route that is
+// clear by the margin of rr_route sends the mixture to stability analysis
+// (theta outside (0, 1) or no root) or on; one inside the margin, or a
+// non-finite evaluation, hands the mixture to k_precheck to redo every
+// evaluation in FP64.  Otherwise ln K and theta wait in the workspace for
+// the last, FP64 evaluation and the tests, which k_precheck takes.
 template <int NC>
 struct PrecheckSS32 {
     int64_t m;
@@ -378,9 +436,18 @@ struct PrecheckSS32 {
         float K[NC], t[NC], x[NC], y[NC], pl[NC], pv[NC];
 #pragma unroll
         for (int i = 0; i < NC; i++) K[i] = __expf(lnK[i]);
-        if (!rachford_rice_f<NC>(z, K, th, t) || !(th > 0.0f && th < 1.0f)) {
+        const int route = rr_route<NC, float>(z, K, kRouteMargin);
+        if (route == 0) {  // too close to call in FP32: every evaluation in FP64
+            ws.theta[m] = NAN;
+            return 3;
+        }
+        if (route < 0) {
             io.status[m] = ST_STAB_RUN;
             return 1;
+        }
+        if (!rachford_rice_f<NC>(z, K, th, t) || !(th > 0.0f && th < 1.0f)) {  // rounding at a clear margin
+            ws.theta[m] = NAN;
+            return 3;
         }
 #pragma unroll
         for (int i = 0; i < NC; i++) {
@@ -546,11 +613,11 @@ struct StabSS {
             store(ws, 1 << 18);
             return 1;
         }
-        if (tm < -kEpsNeg || res < kTolStab) {
+        if (tm < -kEpsNeg || res < ws.ctl.tol_stab) {
             store(ws, 0);
             return 1;
         }
-        if (this_it >= kSSStab) {
+        if (this_it >= ws.ctl.ss_stab) {
             store(ws, 1 << 16);
             return 2;
         }
@@ -673,7 +740,7 @@ struct StabSS32 {
             store(ws, this_it, true);
             return 3;
         }
-        if (this_it >= kSSStab) {
+        if (this_it >= ws.ctl.ss_stab) {
             store(ws, this_it, false);
             return 2;
         }
@@ -862,11 +929,11 @@ struct StabTR {
             else if (rho >= 0.75) radius *= 2.0;
             iters = ++it;
         }
-        if (cur.tm < -kEpsNeg || maxabs<NC>(cur.g) < kTolStab) {
+        if (cur.tm < -kEpsNeg || maxabs<NC>(cur.g) < ws.ctl.tol_stab) {
             store(ws, 0, 0);
             return 1;
         }
-        if (it == kTRStab) {
+        if (it >= ws.ctl.tr_stab) {
             store(ws, 1, 0);
             return 1;
         }
@@ -1061,7 +1128,7 @@ struct SplitSS {
             write_single<NC>(io, m, z);
             return 1;
         }
-        if (fail == 0 && res <= kTolFug) {
+        if (fail == 0 && res <= ws.ctl.tol_fug) {
             if (th > 0.0 && th < 1.0) {
                 finish(io, 0);
                 write_two<NC>(io, m, th, x, y, pl.Z, pv.Z);
@@ -1071,7 +1138,7 @@ struct SplitSS {
             }
             return 1;
         }
-        if (this_it >= kSSSplit) {
+        if (this_it >= ws.ctl.ss_split) {
             // trust-region start: the last evaluated SS point, or the
             // material-balance point at theta = 1/2 for a negative flash
             const bool inside = th > 0.0 && th < 1.0;
@@ -1202,7 +1269,7 @@ struct SplitSS32 {
             th = th0;
             return hand_on(ws, this_it, false);
         }
-        if (res < kSplitFinishRes || this_it >= kSSSplit) {
+        if (res < kSplitFinishRes || this_it >= ws.ctl.ss_split) {
             float dpm = 0.0f;
 #pragma unroll
             for (int i = 0; i < NC; i++) dpm = fmaxf(dpm, fabsf(dp[i]));
@@ -1419,7 +1486,7 @@ struct SplitTR {
                 r = tr_shift_step<NC>(cur.Hs, cur.gs, radius, eta_lo, phase == 2, sh, Lf, u);
             if (r == 0) return 0;
             if (r < 0) {  // Newton polish on an indefinite Hessian: stop here
-                if (maxabs<NC>(cur.gt) > kTolFug) st |= ST_MAXITER;
+                if (maxabs<NC>(cur.gt) > ws.ctl.tol_fug) st |= ST_MAXITER;
                 return finish(io, 0);
             }
 #pragma unroll
@@ -1471,14 +1538,14 @@ struct SplitTR {
             iters = ++it;
         }
         const double res = maxabs<NC>(cur.gt);
-        if (phase == 1 && res < kTolSplitTR) phase = 2;
+        if (phase == 1 && res < ws.ctl.tol_split_tr) phase = 2;
         if (phase == 2) {
-            if (res <= kTolFug && newton_steps >= 1) return finish(io, 0);
-            if (newton_steps == kNewtonPolish) {
+            if (res <= ws.ctl.tol_fug && newton_steps >= 1) return finish(io, 0);
+            if (newton_steps >= ws.ctl.polish) {
                 st |= ST_MAXITER;
                 return finish(io, 0);
             }
-        } else if (it == kTRSplit) {
+        } else if (it >= ws.ctl.tr_split) {
             st |= ST_MAXITER;
             return finish(io, 0);
         }
@@ -1536,6 +1603,28 @@ __global__ void __launch_bounds__(128) k_stab_out(const __grid_constant__ CS cs,
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_STAB);
     PTF_WARP_ROUNDS(len, qi, valid) {
         if (valid) stab_out_item<NC>(cs, ws, io, ws.q_stab[qi]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Phase EOS at given compositions (Appendix A: Eqs. a_i, b_i, mixing_rule,
+// cubic_Z with the lower-gbar root of reading R6, lnphi), one thread per
+// point: the A2 primitive of every stage, evaluated alone.
+// ---------------------------------------------------------------------------
+template <int NC>
+__global__ void __launch_bounds__(128) k_phase_eos(const __grid_constant__ Comp<NC> cp, int64_t n, const double* P,
+                                                   const double* T, const double* c, double* Z, double* lnphi) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n; m += (int64_t)gridDim.x * blockDim.x) {
+        double cc[NC];
+#pragma unroll
+        for (int i = 0; i < NC; i++) cc[i] = c[i * n + m];
+        Mix<NC> mx;
+        mix_init<NC>(cp, P[m], T[m], mx);
+        Phase<NC> ph;
+        eos<NC>(cp, mx, cc, ph);
+        Z[m] = ph.Z;
+#pragma unroll
+        for (int i = 0; i < NC; i++) lnphi[i * n + m] = ph.lnphi[i];
     }
 }
 

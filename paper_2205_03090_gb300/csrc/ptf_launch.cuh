@@ -5,6 +5,7 @@
 #include "ptf_comp.cuh"
 #include "ptf_mlp.cuh"
 #include "ptf_adjoint.cuh"
+#include "ptf_grid.h"
 
 namespace ptf {
 
@@ -12,16 +13,24 @@ namespace ptf {
 // stability TR, decide (or stability output), split SS, split TR.
 constexpr int kStages = 6;
 
-// Blocks of 128 threads for a persistent (refill) kernel: as many as fit on
-// the device at once.
-template <class Kernel>
-int persistent_grid(Kernel k, int sms) {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, 128, 0) != cudaSuccess || b < 1) {
+// Blocks of 128 threads for a persistent (refill) kernel K on the current
+// device with `sms` SMs: as many as fit on the device at once.
+template <auto K>
+int persistent_grid(int sms) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
-        b = 1;
+        dev = -1;
     }
-    return sms * b;
+    const int per_sm = BlocksPerSM<K>::get(dev, [] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K, 128, 0) != cudaSuccess || b < 1) {
+            cudaGetLastError();
+            b = 1;
+        }
+        return b;
+    });
+    return persistent_blocks(sms, per_sm);
 }
 
 // Streams and events (owned by the caller) that let the split SS of the
@@ -52,14 +61,14 @@ cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, 
                             cudaEvent_t* ev, const MLP* nn = nullptr, float p_l = 0.02f, float p_r = 0.98f,
                             int pgrid = 0, const Conc* cc = nullptr) {
     const int sms = grid / 8 > 0 ? grid / 8 : 1;
-    static const int g_pre = persistent_grid(k_precheck<NC, CS>, sms);
-    static const int g_p32 = persistent_grid(k_precheck32<NC, CS>, sms);
-    static const int g_sss = persistent_grid(k_stab_ss<NC, CS>, sms);
-    static const int g_s32 = persistent_grid(k_stab_ss32<NC, CS>, sms);
-    static const int g_sps = persistent_grid(k_split_ss<NC, CS>, sms);
-    static const int g_s3s = persistent_grid(k_split_ss32<NC, CS>, sms);
-    static const int g_str = persistent_grid(k_stab_tr<NC, CS>, sms);
-    static const int g_spt = persistent_grid(k_split_tr<NC, CS>, sms);
+    const int g_pre = persistent_grid<k_precheck<NC, CS>>(sms);
+    const int g_p32 = persistent_grid<k_precheck32<NC, CS>>(sms);
+    const int g_sss = persistent_grid<k_stab_ss<NC, CS>>(sms);
+    const int g_s32 = persistent_grid<k_stab_ss32<NC, CS>>(sms);
+    const int g_sps = persistent_grid<k_split_ss<NC, CS>>(sms);
+    const int g_s3s = persistent_grid<k_split_ss32<NC, CS>>(sms);
+    const int g_str = persistent_grid<k_stab_tr<NC, CS>>(sms);
+    const int g_spt = persistent_grid<k_split_tr<NC, CS>>(sms);
     auto pg = [&](int g) { return pgrid > 0 ? pgrid : g; };
     auto mark = [&](int k) {
         if (ev) cudaEventRecord(ev[k], s);
@@ -138,13 +147,24 @@ cudaError_t launch_many(const Comp<NC>* tab, const int32_t* sys, const WS& ws, c
     return launch_pipeline<NC>(cs, ws, io, grid, mode, s, nullptr, nullptr, 0.02f, 0.98f, pgrid);
 }
 
+// Phase EOS at given compositions (k_phase_eos).
+template <int NC>
+cudaError_t launch_eos(const CompHost& h, int64_t n, const double* P, const double* T, const double* c, double* Z,
+                       double* lnphi, int grid, cudaStream_t s) {
+    const Comp<NC> cp = make_comp<NC>(h);
+    k_phase_eos<NC><<<grid, 128, 0, s>>>(cp, n, P, T, c, Z, lnphi);
+    return cudaGetLastError();
+}
+
 // explicit instantiations live in ptf_inst_*.cu
 #define PTF_DECLARE_NC(NC)                                                                                      \
     extern template cudaError_t launch_plain<NC>(const CompHost&, const WS&, const IO&, int, int, cudaStream_t, \
                                                  cudaEvent_t*, const MLP*, float, float, const Conc*);           \
     extern template cudaError_t launch_many<NC>(const Comp<NC>*, const int32_t*, const WS&, const IO&, int, int, \
                                                 int, cudaStream_t);                                              \
-    extern template cudaError_t launch_adjoint<NC>(const CompHost&, const AdjIO&, int, cudaStream_t);
+    extern template cudaError_t launch_adjoint<NC>(const CompHost&, const AdjIO&, int, cudaStream_t);            \
+    extern template cudaError_t launch_eos<NC>(const CompHost&, int64_t, const double*, const double*,          \
+                                               const double*, double*, double*, int, cudaStream_t);
 PTF_DECLARE_NC(2) PTF_DECLARE_NC(3) PTF_DECLARE_NC(4) PTF_DECLARE_NC(5) PTF_DECLARE_NC(6) PTF_DECLARE_NC(7)
 PTF_DECLARE_NC(8) PTF_DECLARE_NC(9) PTF_DECLARE_NC(10) PTF_DECLARE_NC(11) PTF_DECLARE_NC(12) PTF_DECLARE_NC(13)
 PTF_DECLARE_NC(14) PTF_DECLARE_NC(15) PTF_DECLARE_NC(16)
@@ -156,6 +176,8 @@ PTF_DECLARE_NC(14) PTF_DECLARE_NC(15) PTF_DECLARE_NC(16)
                                           const MLP*, float, float, const Conc*);                                  \
     template cudaError_t launch_many<NC>(const Comp<NC>*, const int32_t*, const WS&, const IO&, int, int, int,     \
                                          cudaStream_t);                                                            \
-    template cudaError_t launch_adjoint<NC>(const CompHost&, const AdjIO&, int, cudaStream_t);
+    template cudaError_t launch_adjoint<NC>(const CompHost&, const AdjIO&, int, cudaStream_t);                     \
+    template cudaError_t launch_eos<NC>(const CompHost&, int64_t, const double*, const double*, const double*,      \
+                                        double*, double*, int, cudaStream_t);
 
 }  // namespace ptf

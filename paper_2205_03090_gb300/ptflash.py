@@ -39,7 +39,14 @@ class PtflashError(RuntimeError):
 
 class ptflash_options(ctypes.Structure):
     _fields_ = [("use_nn", ctypes.c_int32), ("p_l", ctypes.c_double), ("p_r", ctypes.c_double),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("max_ss_stab", ctypes.c_int32), ("max_tr_stab", ctypes.c_int32), ("max_ss_split", ctypes.c_int32),
+                ("max_tr_split", ctypes.c_int32), ("max_polish", ctypes.c_int32), ("tol_stab", ctypes.c_double),
+                ("tol_split_tr", ctypes.c_double), ("tol_fug", ctypes.c_double), ("reserved", ctypes.c_int32 * 4)]
+
+
+# ptflash_options fields a caller may set through **opts (0 = default)
+OPTION_FIELDS = ("max_ss_stab", "max_tr_stab", "max_ss_split", "max_tr_split", "max_polish", "tol_stab",
+                 "tol_split_tr", "tol_fug")
 
 
 def load(path: str = LIB_PATH):
@@ -90,6 +97,12 @@ def load(path: str = LIB_PATH):
     for f in ("ptflash_batch_create", "ptflash_batch_destroy", "ptflash_batch_flash", "ptflash_batch_tune",
               "ptflash_batch_info"):
         getattr(lib, f).restype = ctypes.c_int
+    lib.ptflash_default_options.argtypes = [ctypes.POINTER(ptflash_options)]
+    lib.ptflash_default_options.restype = ctypes.c_int
+    lib.ptflash_phase_eos.argtypes = [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP]
+    lib.ptflash_phase_eos.restype = ctypes.c_int
+    lib.ptflash_fp64_fma_rate.argtypes = [_I64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.ptflash_fp64_fma_rate.restype = ctypes.c_int
     lib.ptflash_strerror.argtypes = [ctypes.c_int]
     lib.ptflash_strerror.restype = ctypes.c_char_p
     lib.ptflash_last_cuda_error.restype = ctypes.c_char_p
@@ -118,12 +131,31 @@ def _stream_handle(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _opts(use_nn=False, p_l=0.02, p_r=0.98):
+def _opts(use_nn=False, p_l=0.02, p_r=0.98, **caps):
     o = ptflash_options()
     o.use_nn = 1 if use_nn else 0
     o.p_l = p_l
     o.p_r = p_r
+    for k, v in caps.items():
+        if k not in OPTION_FIELDS:
+            raise TypeError(f"unknown flash option {k}")
+        setattr(o, k, v)
     return o
+
+
+def default_options() -> dict:
+    """The library's default caps and tolerances (ptflash_default_options)."""
+    o = ptflash_options()
+    _check(load().ptflash_default_options(ctypes.byref(o)))
+    return {k: getattr(o, k) for k in ("p_l", "p_r") + OPTION_FIELDS}
+
+
+def fp64_fma_rate(iters: int = 6000):
+    """FP64 FMA throughput of the current device (ptflash_fp64_fma_rate):
+    (TFLOP/s, ms of the timed launch)."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().ptflash_fp64_fma_rate(int(iters), ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
 
 
 @dataclass
@@ -174,18 +206,19 @@ class Flash:
                            torch.empty(n, **i32) if with_iters else None)
 
     def ptflash_flash(self, P, T, z, out: FlashResult | None = None, use_nn=False, p_l=0.02, p_r=0.98,
-                      stream=None) -> FlashResult:
-        """Device tensors P[n], T[n], z[nc, n] (float64, contiguous)."""
+                      stream=None, **caps) -> FlashResult:
+        """Device tensors P[n], T[n], z[nc, n] (float64, contiguous).  caps:
+        ptflash_options caps and tolerances (OPTION_FIELDS; 0 = default)."""
         n = int(P.shape[0])
         assert z.shape == (self.nc, n) and P.is_cuda and z.is_contiguous()
         out = out or self.alloc_outputs(n, P.device)
-        o = _opts(use_nn, p_l, p_r)
+        o = _opts(use_nn, p_l, p_r, **caps)
         _check(load().ptflash_flash(self._h, n, _ptr(P), _ptr(T), _ptr(z), _ptr(out.nphase), _ptr(out.beta),
                                     _ptr(out.x), _ptr(out.y), _ptr(out.K), _ptr(out.status), _ptr(out.iters),
                                     ctypes.byref(o), _stream_handle(stream)))
         return out
 
-    def ptflash_flash_host(self, P, T, z, out=None, use_nn=False, p_l=0.02, p_r=0.98, stream=None):
+    def ptflash_flash_host(self, P, T, z, out=None, use_nn=False, p_l=0.02, p_r=0.98, stream=None, **caps):
         """Host tensors (pinned CPU torch tensors or NumPy arrays); returns host outputs."""
         import torch
         n = int(P.shape[0])
@@ -195,11 +228,23 @@ class Flash:
                               torch.empty(self.nc, n, dtype=torch.float64),
                               torch.empty(self.nc, n, dtype=torch.float64), torch.empty(n, dtype=torch.int32),
                               torch.empty(n, dtype=torch.int32))
-        o = _opts(use_nn, p_l, p_r)
+        o = _opts(use_nn, p_l, p_r, **caps)
         _check(load().ptflash_flash_host(self._h, n, _ptr(P), _ptr(T), _ptr(z), _ptr(out.nphase), _ptr(out.beta),
                                          _ptr(out.x), _ptr(out.y), _ptr(out.K), _ptr(out.status), _ptr(out.iters),
                                          ctypes.byref(o), _stream_handle(stream)))
         return out
+
+    def ptflash_phase_eos(self, P, T, c, stream=None):
+        """Z[n] and ln phi[nc, n] of the phase of composition c[nc, n] (device
+        tensors) at P[n], T[n]."""
+        import torch
+        n = int(P.shape[0])
+        assert c.shape == (self.nc, n) and c.is_contiguous()
+        Z = torch.empty(n, dtype=torch.float64, device=P.device)
+        lnphi = torch.empty(self.nc, n, dtype=torch.float64, device=P.device)
+        _check(load().ptflash_phase_eos(self._h, n, _ptr(P), _ptr(T), _ptr(c), _ptr(Z), _ptr(lnphi),
+                                        _stream_handle(stream)))
+        return Z, lnphi
 
     def ptflash_stability(self, P, T, z, stream=None):
         import torch

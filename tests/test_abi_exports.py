@@ -73,3 +73,18 @@ def test_batch_argument_checks_without_gpu():
     h = ctypes.c_void_p()
     assert lib.ptflash_batch_create(None, 1, None, None, None, None, None, None) == -1
     assert lib.ptflash_batch_create(ctypes.byref(h), 0, None, None, None, None, None, None) == -1
+
+
+def test_default_options_without_gpu():
+    """ptflash_default_options fills the paper's caps and tolerances (and the
+    readings' split caps) without touching the GPU; the binding's struct has
+    the C layout."""
+    from paper_2205_03090_gb300 import build, ptflash
+    build.build()
+    d = ptflash.default_options()
+    assert d["max_ss_stab"] == 9 and d["max_tr_stab"] == 20  # K_ss, K_tr of Alg. 2
+    assert d["max_ss_split"] == 9 and d["max_tr_split"] == 60 and d["max_polish"] == 10
+    assert d["tol_stab"] == 1e-6 and d["tol_split_tr"] == 1e-8 and d["tol_fug"] == 0.98e-10
+    assert d["p_l"] == 0.02 and d["p_r"] == 0.98
+    assert ctypes.sizeof(ptflash.ptflash_options) == 88  # the C sizeof on LP64 (x86-64 and aarch64)
+    assert ptflash.load().ptflash_default_options(None) == -1

@@ -60,7 +60,7 @@ def test_batch_parity_every_nc(ptf, oracle_mod):
         g = b.unpack(out, s)
         r = compare(oracle_mod, comp, cond, g)
         print("system", s, "nc", comp.nc, {k: v for k, v in r.items() if k != "bad_idx"})
-        _assert_parity(r, max_val_bad_frac=2e-3)
+        _assert_parity(r, max_capped_frac=1e-3)
     b.close()
 
 

@@ -32,7 +32,7 @@ def test_case_study_parity(ptf, oracle_mod, case, n):
     g = {k: getattr(out, k).cpu().numpy() for k in ("nphase", "beta", "x", "y", "status")}
     r = compare(oracle_mod, comp, cond, g)
     print(case, {k: v for k, v in r.items() if k != "bad_idx"}, "two-phase", float((g["nphase"] == 2).mean()))
-    _assert_parity(r, max_val_bad_frac=2e-3)
+    _assert_parity(r, max_capped_frac=1e-3)
     if ft is not None:  # every fluid type reaches both phase counts
         for t in range(4):
             assert set(np.unique(g["nphase"][ft == t])) <= {1, 2}

@@ -5,7 +5,9 @@ identical wherever the oracle's fully converged min tpd satisfies
 |tpd| > 1e-8; where both sides report two phases, |d beta|, |d x|, |d y|
 <= 1e-8; every GPU two-phase result has fugacity residual <= 1e-10 when its
 x and y are re-evaluated by the oracle's EOS, and satisfies the material
-balance.
+balance; the precheck routes every mixture the way the oracle does.  The
+only allowance is for runs that stop at an iteration cap (status MAXITER on
+either side): their outputs are not equilibria, and each is printed.
 """
 import numpy as np
 import pytest
@@ -52,7 +54,7 @@ def _fug_residual(oracle_mod, s, P, T, x, y):
     return np.abs(np.log(y) + ly - np.log(x) - lx).max()
 
 
-def compare(oracle_mod, comp, cond, g, idx=None, fug_checks=400):
+def compare(oracle_mod, comp, cond, g, idx=None, fug_checks=100_000):
     """Compare GPU results g (all n) with the oracle on indices idx."""
     s = oracle_mod.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
     if idx is None:
@@ -61,6 +63,8 @@ def compare(oracle_mod, comp, cond, g, idx=None, fug_checks=400):
     o = oracle_mod.flash(s, P, T, z)
     tp = oracle_mod.tpd_min(s, P, T, z)
     gn, gb, gx, gy = g["nphase"][idx], g["beta"][idx], g["x"][:, idx], g["y"][:, idx]
+    gst = g["status"][idx]
+    capped = ((gst | o["status"]) & 16) != 0  # MAXITER on either side
     graded = np.abs(tp) > 1e-8
     lab_bad = graded & (gn != o["nphase"])
     both = (gn == 2) & (o["nphase"] == 2)
@@ -72,23 +76,31 @@ def compare(oracle_mod, comp, cond, g, idx=None, fug_checks=400):
     two = np.nonzero(gn == 2)[0]
     mb = np.abs(gx[:, two] * (1 - gb[two]) + gy[:, two] * gb[two] - z[:, two]).max() if len(two) else 0.0
     fres = [_fug_residual(oracle_mod, s, P[k], T[k], gx[:, k], gy[:, k]) for k in two[:fug_checks]
-            if not (g["status"][idx][k] & 16)]
+            if not (gst[k] & 16)]
     route_mask = 1 | 2  # precheck-unstable / stability-run routing bits
-    route_same = ((g["status"][idx] & route_mask) == (o["status"] & route_mask)).mean()
-    return dict(n=len(idx), graded=int(graded.sum()), label_bad=int(lab_bad.sum()), both=int(both.sum()),
-                val_bad=int(val_bad.sum()), max_db=float(db[both].max()) if both.any() else 0.0,
-                max_dx=float(dx[both].max()) if both.any() else 0.0,
-                max_dy=float(dy[both].max()) if both.any() else 0.0, mass_balance=float(mb),
-                max_fug=float(max(fres)) if fres else 0.0, route_same=float(route_same),
-                bad_idx=np.nonzero(lab_bad | val_bad)[0])
+    route_diff = (gst & route_mask) != (o["status"] & route_mask)
+    miss = np.nonzero((lab_bad | val_bad) & capped)[0]
+    for k in miss:  # the allowance, each with its cause
+        print(f"  capped miss {idx[k]}: status gpu {gst[k]} oracle {o['status'][k]}, nphase {gn[k]}/{o['nphase'][k]}, "
+              f"|min tpd| {abs(tp[k]):.2e}, dbeta {db[k]:.2e}")
+    return dict(n=len(idx), graded=int(graded.sum()), label_bad=int((lab_bad & ~capped).sum()),
+                both=int(both.sum()), val_bad=int((val_bad & ~capped).sum()), capped_misses=len(miss),
+                capped=int(capped.sum()), max_db=float(db[both & ~capped].max()) if (both & ~capped).any() else 0.0,
+                max_dx=float(dx[both & ~capped].max()) if (both & ~capped).any() else 0.0,
+                max_dy=float(dy[both & ~capped].max()) if (both & ~capped).any() else 0.0, mass_balance=float(mb),
+                max_fug=float(max(fres)) if fres else 0.0, route_diff=int((route_diff & ~capped).sum()),
+                bad_idx=np.nonzero((lab_bad | val_bad | route_diff) & ~capped)[0])
 
 
-def _assert_parity(r, max_val_bad_frac=0.0):
+def _assert_parity(r, max_capped_frac=1e-4):
+    """No miss outside MAXITER runs, every route as the oracle's, and at most
+    a fraction max_capped_frac of the mixtures stopped at a cap."""
     assert r["label_bad"] == 0, r
-    assert r["val_bad"] <= max_val_bad_frac * max(1, r["both"]), r
+    assert r["val_bad"] == 0, r
+    assert r["route_diff"] == 0, r
+    assert r["capped"] <= max_capped_frac * r["n"], r
     assert r["mass_balance"] < 1e-12, r
     assert r["max_fug"] <= TOL_FUG, r
-    assert r["route_same"] > 0.999, r
 
 
 def test_parity_nc3_full(ptf, oracle_mod):
@@ -107,7 +119,7 @@ def test_parity_nc8_subset(ptf, oracle_mod):
     g = _gpu_flash(ptf, comp, cond)
     r = compare(oracle_mod, comp, cond, g)
     print("nc8", {k: v for k, v in r.items() if k != "bad_idx"})
-    _assert_parity(r, max_val_bad_frac=1e-3)
+    _assert_parity(r)
 
 
 def test_parity_nc10_subset(ptf, oracle_mod):
@@ -115,7 +127,7 @@ def test_parity_nc10_subset(ptf, oracle_mod):
     g = _gpu_flash(ptf, comp, cond)
     r = compare(oracle_mod, comp, cond, g)
     print("nc10", {k: v for k, v in r.items() if k != "bad_idx"})
-    _assert_parity(r, max_val_bad_frac=1e-3)
+    _assert_parity(r)
 
 
 def test_parity_full_size_sampled(ptf, oracle_mod):
@@ -127,7 +139,7 @@ def test_parity_full_size_sampled(ptf, oracle_mod):
     idx = np.sort(rng.choice(cond.n, 3000, replace=False))
     r = compare(oracle_mod, comp, cond, g, idx=idx)
     print("nc8 full sampled", {k: v for k, v in r.items() if k != "bad_idx"}, g["counts"])
-    _assert_parity(r, max_val_bad_frac=1e-3)
+    _assert_parity(r)
     # properties that hold at any size: statuses finite, outputs finite
     assert (g["status"] & 64).sum() == 0
     assert np.isfinite(g["beta"]).all() and np.isfinite(g["x"]).all()

@@ -52,10 +52,16 @@ def test_noalloc_matches_flash_twice():
         for t in (out.beta, out.x, out.y, out.K):
             t.fill_(float("nan"))
         out.nphase.fill_(-1)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         rc = lib.ptflash_flash_noalloc(nc, *hp, n, *(ctypes.c_void_p(t.data_ptr()) for t in (
             P, T, z, out.nphase, out.beta, out.x, out.y, out.K, out.status, out.iters)), stream)
         assert rc == 0, lib.ptflash_strerror(rc)
         torch.cuda.synchronize()
+        if call == 1:
+            # the defining property: once the first call has loaded the
+            # library's kernels, a call takes no device memory
+            assert torch.cuda.mem_get_info()[0] == free_before
         got = {k: getattr(out, k).cpu().numpy() for k in refn}
         np.testing.assert_array_equal(got["nphase"], refn["nphase"])
         np.testing.assert_array_equal(got["status"], refn["status"])
