@@ -334,6 +334,7 @@ def paper_learned_leg(args, rank, dev, flush, stream):
     comp, cond, ft = wl.paper_case("c9", n, 300 + rank)
     fl = ptflash.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=n)
     meta = nn.load_checkpoint(fl, train_paper_nn.DEFAULT_OUT)
+    p_l, p_r = nn.thresholds(meta)
     P = torch.tensor(cond.P, device=dev)
     T = torch.tensor(cond.T, device=dev)
     z = torch.tensor(cond.z, device=dev).contiguous()
@@ -348,7 +349,7 @@ def paper_learned_leg(args, rank, dev, flush, stream):
             e1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            fl.ptflash_flash(P, T, z, out=out, use_nn=use, stream=stream)
+            fl.ptflash_flash(P, T, z, out=out, use_nn=use, p_l=p_l, p_r=p_r, stream=stream)
             e1.record(stream)
             torch.cuda.synchronize()
             if it >= args.warmup:
@@ -359,6 +360,7 @@ def paper_learned_leg(args, rank, dev, flush, stream):
                      "split_ss_converged_frac": 1.0 - q["split_tr"] / max(1, q["split"])}
         if use:
             res[form]["classifier_decided_frac"] = float(((st & (128 | 256)) != 0).mean())
+            res[form]["rejected_frac"] = float(((st & 1024) != 0).mean())
             g = {k: getattr(out, k).cpu().numpy() for k in ("nphase", "beta", "x", "y", "status")}
     frac, sample = float("nan"), 0
     if rank == 0 and args.cpu_sample > 0:
@@ -375,6 +377,7 @@ def paper_learned_leg(args, rank, dev, flush, stream):
             "speedup_vs_plain": res["plain"]["ms_per_step"] / res["learned"]["ms_per_step"],
             "oracle_match": {"frac": frac, "sample": sample, "tol": TOL}, "plain": res["plain"],
             "learned": res["learned"], "networks": {k: meta.get(k) for k in ("classifier", "initializer")},
+            "thresholds": {"p_l": p_l, "p_r": p_r},
             "paper_table5_context": PAPER_TABLE5}
 
 
@@ -388,10 +391,11 @@ def run_oracle_sample(comp, cond, idx, nthreads=None):
     return o, dt, s
 
 
-def match_fraction(s, comp, cond, idx, o, g):
+def match_fraction(s, comp, cond, idx, o, g, misses=None):
     """Fraction of sampled flashes matching the oracle (label exact where the
     oracle's fully converged |min tpd| > 1e-8; beta, x, y within 1e-8 where
-    both are two-phase)."""
+    both are two-phase).  misses (a list), if given, receives up to 20
+    records of the mismatches: index, both statuses, phase counts, |dbeta|."""
     import oracle
     gn, gb = g["nphase"][idx], g["beta"][idx]
     gx, gy = g["x"][:, idx], g["y"][:, idx]
@@ -403,6 +407,11 @@ def match_fraction(s, comp, cond, idx, o, g):
     if len(diff):
         tp = oracle.tpd_min(s, cond.P[idx][diff], cond.T[idx][diff], np.ascontiguousarray(cond.z[:, idx][:, diff]))
         ok[diff[np.abs(tp) > 1e-8]] = False
+    if misses is not None:
+        for k in np.nonzero(~ok)[0][:20]:
+            misses.append({"mixture": int(idx[k]), "status": int(g["status"][idx[k]]), "status_oracle": int(o["status"][k]),
+                           "nphase": int(gn[k]), "nphase_oracle": int(o["nphase"][k]),
+                           "dbeta": float(abs(gb[k] - o["beta"][k]))})
     return float(ok.mean())
 
 
@@ -549,10 +558,11 @@ def ours_arm(args, ws, rank, local):
         o, cpu_dt, s = run_oracle_sample(comp, cond, idx)
         import oracle as _or
         cores = _or.default_threads()
-        frac = match_fraction(s, comp, cond, idx, o, g)
+        misses = []
+        frac = match_fraction(s, comp, cond, idx, o, g, misses)
         ops_per_flash = o["ops"] / sample  # [oracle stage, kind]
     else:
-        cpu_dt, cores, frac, ops_per_flash = float("nan"), 0, float("nan"), np.full((5, 5), np.nan)
+        cpu_dt, cores, frac, ops_per_flash, misses = float("nan"), 0, float("nan"), np.full((5, 5), np.nan), []
 
     mean_stage = {k: float(np.mean([d[k] for d in stage_ms])) for k in LIB_STAGES}
     dom = max(mean_stage, key=mean_stage.get)
@@ -580,7 +590,7 @@ def ours_arm(args, ws, rank, local):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "n": n, "nc": nc, "form": "plain", "parallelism": f"replicas{ws}",
                    "l2": "flushed between steps (512 MB write); inputs resident in HBM"},
-        "oracle_match": {"frac": frac, "sample": sample, "tol": TOL},
+        "oracle_match": {"frac": frac, "sample": sample, "tol": TOL, "misses": misses},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "traffic_source": traffic_src,
@@ -636,6 +646,7 @@ def learned_leg(args, rank, dev, flush, stream):
         train_nn.main([])
     fl = ptflash.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=n)
     meta = nn.load_checkpoint(fl, train_nn.DEFAULT_OUT)
+    p_l, p_r = nn.thresholds(meta)
     P = torch.tensor(cond.P, device=dev)
     T = torch.tensor(cond.T, device=dev)
     z = torch.tensor(cond.z, device=dev).contiguous()
@@ -644,7 +655,7 @@ def learned_leg(args, rank, dev, flush, stream):
     for form in ("plain", "learned"):
         use = form == "learned"
         for _ in range(max(1, args.warmup - 1)):
-            fl.ptflash_flash(P, T, z, out=out, use_nn=use, stream=stream)
+            fl.ptflash_flash(P, T, z, out=out, use_nn=use, p_l=p_l, p_r=p_r, stream=stream)
         ms = []
         for _ in range(max(1, args.steps)):
             flush.zero_()
@@ -652,20 +663,24 @@ def learned_leg(args, rank, dev, flush, stream):
             e1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            fl.ptflash_flash(P, T, z, out=out, use_nn=use, stream=stream)
+            fl.ptflash_flash(P, T, z, out=out, use_nn=use, p_l=p_l, p_r=p_r, stream=stream)
             e1.record(stream)
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
         res[form] = {"ms_per_step": float(np.mean(ms)), "queues": fl.ptflash_last_counts()}
         if use:
             g = {k: getattr(out, k).cpu().numpy() for k in ("nphase", "beta", "x", "y", "status")}
-    frac, sample = float("nan"), 0
+            st = g["status"]
+            res[form]["routes"] = {"nn_stable": float(((st & 128) != 0).mean()),
+                                   "nn_unstable": float(((st & 256) != 0).mean()),
+                                   "rejected": float(((st & 1024) != 0).mean())}
+    frac, sample, misses = float("nan"), 0, []
     if rank == 0 and args.cpu_sample > 0:
         rng = np.random.default_rng(13)
-        sample = min(n, max(2000, args.cpu_sample // 5))
+        sample = min(n, max(40_000, args.cpu_sample // 5))
         idx = np.sort(rng.choice(n, sample, replace=False))
         o, _, s = run_oracle_sample(comp, cond, idx)
-        frac = match_fraction(s, comp, cond, idx, o, g)
+        frac = match_fraction(s, comp, cond, idx, o, g, misses)
     fl.close()
     learned_v = n * (frac if frac == frac else 1.0) / (res["learned"]["ms_per_step"] / 1e3)
     return {"workload": LEARNED_DESC, "n": n, "ms_per_step": res["learned"]["ms_per_step"],
@@ -673,8 +688,9 @@ def learned_leg(args, rank, dev, flush, stream):
             "plain_ms_per_step": res["plain"]["ms_per_step"],
             "plain_value": n / (res["plain"]["ms_per_step"] / 1e3),
             "speedup_vs_plain": res["plain"]["ms_per_step"] / res["learned"]["ms_per_step"],
-            "oracle_match": {"frac": frac, "sample": sample, "tol": TOL},
+            "oracle_match": {"frac": frac, "sample": sample, "tol": TOL, "misses": misses},
             "queues_plain": res["plain"]["queues"], "queues_learned": res["learned"]["queues"],
+            "routes": res["learned"]["routes"], "thresholds": {"p_l": p_l, "p_r": p_r},
             "networks": {k: meta.get(k) for k in ("classifier", "initializer", "train_samples")}}
 
 

@@ -65,6 +65,7 @@ extern "C" {
 #define PTF_ST_NN_STABLE 128       /* learned form: classifier said stable (p >= p_r) */
 #define PTF_ST_NN_UNSTABLE 256     /* learned form: classifier said unstable (p <= p_l) */
 #define PTF_ST_NN_INIT 512         /* learned form: K initialised by the initializer network */
+#define PTF_ST_NN_REJECTED 1024    /* learned form: the plain method rejected the network route and redid the flash */
 
 typedef struct ptflash_ctx ptflash_ctx;
 
@@ -89,7 +90,10 @@ typedef struct {
     double tol_fug;       /* split convergence: max_i |ln y_i + ln phi_i^V - ln x_i - ln phi_i^L|
                              (default 0.98e-10: 2 % below the 1e-10 target, so that the target
                              holds when another FP64 implementation re-evaluates the point) */
-    int32_t reserved[4];
+    double nn_lnk_dev;    /* learned form: a split started from the initializer's K is kept only if every
+                             converged ln K_i lies within this distance of the network's (default 0.3);
+                             otherwise the plain method redoes the mixture */
+    int32_t reserved[2];
 } ptflash_options;
 
 /* Fill *opt with the defaults (plain method).  PTF_ERR_INVALID_ARG if NULL. */
@@ -119,7 +123,20 @@ int ptflash_set_components(ptflash_ctx* ctx, int nc, const double* Tc, const dou
 
 /*
  * Isothermal two-phase flash of n mixtures (Sec. 2.2.3; the learned form of
- * Sec. 4.3 when opt->use_nn = 1).  DEVICE arrays: P[n], T[n], z[nc*n]
+ * Sec. 4.3 when opt->use_nn = 1).
+ * Learned form: the classifier's probability p of stability routes each
+ * mixture.  p >= p_r: single phase (NN_STABLE) unless tpd is negative at one
+ * of the trial phases z K, z / K of the initializer's K and of Wilson K, which
+ * proves instability and sends the mixture down the plain route.  p <= p_l
+ * (initializer K bracketing 1, NN_UNSTABLE): the plain precheck runs; if it
+ * proves instability the split starts from the initializer's K, else the
+ * mixture continues down the plain route.  A split from the initializer's K
+ * is kept only if it converges (within the paper's 20 trust-region
+ * iterations) to two phases with Delta G < 0 and its ln K within
+ * opt->nn_lnk_dev of the network's; otherwise the plain method redoes the
+ * mixture (NN_REJECTED).  Every other mixture takes the plain route:
+ * precheck, stability analysis from Wilson K, split.
+ * DEVICE arrays: P[n], T[n], z[nc*n]
  * inputs; nphase[n], beta[n], x[nc*n], y[nc*n], K[nc*n], status[n] outputs;
  * iters[n] optional (NULL to skip): packed iteration counts
  * split SS | split TR << 8 | stability SS << 16 | stability TR << 24

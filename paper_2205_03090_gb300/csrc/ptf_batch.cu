@@ -73,7 +73,7 @@ struct Group {
     SysDesc* desc = nullptr;      // device [sys.size()]
     int32_t* sys_of = nullptr;    // device [N]
     double* wsd = nullptr;        // workspace doubles, (8 nc + 3) N
-    int32_t* wsi = nullptr;       // workspace ints, 7 N + 64
+    int32_t* wsi = nullptr;       // workspace ints, 8 N + 64
     double* sd = nullptr;         // staging doubles: P, T [N]; z, x, y, K [nc N]; beta [N]
     int32_t* si = nullptr;        // staging ints: nphase, status, iters [N]
     cudaStream_t st = nullptr;
@@ -101,6 +101,7 @@ struct Group {
         w.q_split = q; q += N;
         w.q_stab_tr = q; q += 2 * N;
         w.q_split_tr = q; q += N;
+        w.q_sort = q; q += N;
         return w;
     }
     IO io() const {
@@ -331,7 +332,7 @@ int ptflash_batch_create(ptflash_batch** out, int nsys, const int32_t* nc, const
         if ((e = cudaMalloc(&G.desc, d.size() * sizeof(SysDesc))) != cudaSuccess) break;
         if ((e = cudaMalloc(&G.sys_of, N_ * sizeof(int32_t))) != cudaSuccess) break;
         if ((e = cudaMalloc(&G.wsd, (size_t)(8 * k + 3) * N_ * sizeof(double))) != cudaSuccess) break;
-        if ((e = cudaMalloc(&G.wsi, (size_t)(7 * N_ + 64) * sizeof(int32_t))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&G.wsi, (size_t)(8 * N_ + 64) * sizeof(int32_t))) != cudaSuccess) break;
         if ((e = cudaMalloc(&G.sd, (size_t)(4 * k + 3) * N_ * sizeof(double))) != cudaSuccess) break;
         if ((e = cudaMalloc(&G.si, (size_t)3 * N_ * sizeof(int32_t))) != cudaSuccess) break;
         if ((e = cudaStreamCreateWithFlags(&G.st, cudaStreamNonBlocking)) != cudaSuccess) break;

@@ -25,13 +25,6 @@ int cuda_fail(cudaError_t e) {
     } while (0)
 }  // namespace
 
-// Fold the four queue counters of a chunk into the call's accumulator (the
-// split queue is counted from both of its ends).
-__global__ void k_fold_counts(const int32_t* cnt, unsigned long long* acc) {
-    if (threadIdx.x < 4)
-        acc[threadIdx.x] += (unsigned long long)cnt[threadIdx.x] + (threadIdx.x == Q_SPLIT ? cnt[Q_SPLIT_B] : 0);
-}
-
 static cudaError_t dispatch(ptflash_ctx* c, const WS& ws, const IO& io, int mode, cudaStream_t s, float p_l = 0.02f,
                            float p_r = 0.98f) {
     const int grid = c->sm_count * 8;
@@ -193,7 +186,7 @@ int ptflash_create(ptflash_ctx** out, int nc_max, int64_t n_max) {
         delete c;
         return cuda_fail(e);
     }
-    size_t nd = (size_t)(8 * nc_max + 3) * (size_t)n_max, ni = 7 * (size_t)n_max + 64;
+    size_t nd = (size_t)(8 * nc_max + 3) * (size_t)n_max, ni = 9 * (size_t)n_max + 64;
     if (cudaMalloc(&c->wsd, nd * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->wsi, ni * sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&c->acc, 8 * sizeof(unsigned long long)) != cudaSuccess) {
@@ -291,7 +284,8 @@ static int parse_options(const ptflash_ctx* c, const ptflash_options* opt, CallO
     if (!cap(opt->max_ss_stab, o.ctl.ss_stab) || !cap(opt->max_tr_stab, o.ctl.tr_stab) ||
         !cap(opt->max_ss_split, o.ctl.ss_split) || !cap(opt->max_tr_split, o.ctl.tr_split) ||
         !cap(opt->max_polish, o.ctl.polish) || !tol(opt->tol_stab, o.ctl.tol_stab) ||
-        !tol(opt->tol_split_tr, o.ctl.tol_split_tr) || !tol(opt->tol_fug, o.ctl.tol_fug))
+        !tol(opt->tol_split_tr, o.ctl.tol_split_tr) || !tol(opt->tol_fug, o.ctl.tol_fug) ||
+        !tol(opt->nn_lnk_dev, o.ctl.nn_lnk_dev))
         return PTF_ERR_INVALID_ARG;
     if (opt->use_nn) {
         if (!(opt->p_l >= 0.0 && opt->p_l <= opt->p_r && opt->p_r <= 1.0)) return PTF_ERR_INVALID_ARG;
@@ -370,6 +364,7 @@ int ptflash_default_options(ptflash_options* opt) {
     opt->tol_stab = d.tol_stab;
     opt->tol_split_tr = d.tol_split_tr;
     opt->tol_fug = d.tol_fug;
+    opt->nn_lnk_dev = d.nn_lnk_dev;
     return PTF_OK;
 }
 

@@ -37,7 +37,7 @@ struct ptflash_ctx {
     bool have_comp = false;
     // device scratch
     double* wsd = nullptr;    // (8 nc_max + 3) n_max doubles
-    int32_t* wsi = nullptr;   // 7 n_max + 64 int32
+    int32_t* wsi = nullptr;   // 9 n_max + 64 int32
     // staging for the host-pointer entry point
     double* hd = nullptr;     // (4 nc_max + 3) n_max doubles: P, T, z, beta, x, y, K
     int32_t* hi = nullptr;    // 3 n_max: nphase, status, iters
@@ -75,6 +75,9 @@ inline ptf::WS make_ws(ptflash_ctx* c, int64_t n) {
     w.q_split = q; q += n;
     w.q_stab_tr = q; q += 2 * n;
     w.q_split_tr = q; q += n;
+    w.q_redo = q; q += n;
+    w.q_sort = q; q += n;
+    w.acc = c->acc;
     w.nnp = c->nnbuf;
     w.nnk = c->nnbuf ? c->nnbuf + n : nullptr;
     return w;

@@ -43,6 +43,11 @@ constexpr int kPrecheck = 3;          // Sec. 2.2.3
 constexpr double kEpsNeg = 1e-10;     // "negative" tm / tpd / Delta G
 constexpr double kTrivialLnK = 1e-6;  // split collapsed to K = 1
 constexpr double kPredTrust = 1e-12;  // ratio test trusted above this
+// Learned form: a split started from the initializer's K keeps its result only
+// if its converged ln K lie within this distance of the network's prediction
+// (farther away, the split went to a stationary point other than the one the
+// network was trained on, and the plain method redoes the mixture).
+constexpr double kNNLnKDev = 0.3;
 
 // Tolerances and iteration caps of one call (ptflash_options; the defaults
 // above).  Part of the workspace descriptor, a kernel parameter, so every
@@ -50,6 +55,7 @@ constexpr double kPredTrust = 1e-12;  // ratio test trusted above this
 struct Ctl {
     int ss_stab = kSSStab, tr_stab = kTRStab, ss_split = kSSSplit, tr_split = kTRSplit, polish = kNewtonPolish;
     double tol_stab = kTolStab, tol_split_tr = kTolSplitTR, tol_fug = kTolFug;
+    double nn_lnk_dev = kNNLnKDev;  // learned form: accepted max |ln K - ln K_net| of a network-started split
 };
 
 // status bits (same values as documented in include/ptflash.h)
@@ -63,6 +69,7 @@ constexpr int ST_NONFINITE = 64;
 constexpr int ST_NN_STABLE = 128;
 constexpr int ST_NN_UNSTABLE = 256;
 constexpr int ST_NN_INIT = 512;
+constexpr int ST_NN_REJECT = 1024;
 
 // Component table, passed by value as a kernel parameter (constant bank:
 // every access is a uniform broadcast).
@@ -372,10 +379,16 @@ template <int NC>
 __device__ __forceinline__ void dlnphi_dn(const Comp<NC>& cp, const Mix<NC>& mx, const double* c, const Phase<NC>& ph,
                                           double* J) {
     const double A = ph.A, B = ph.B, Z = ph.Z, L = ph.L;
-    const double invB = 1.0 / B, invZB = 1.0 / (Z - B), invZpB = 1.0 / (Z + B), invZ = 1.0 / Z;
     const double FZ = fma(fma(3.0, Z, -2.0), Z, A - B - B * B);
     const double FA = Z - B, FB = -Z - 2.0 * B * Z - A;
-    const double invFZ = 1.0 / FZ;
+    // the five reciprocals 1/B, 1/(Z-B), 1/(Z+B), 1/Z, 1/FZ from one division
+    // (each product of the others and the reciprocal of the whole product)
+    const double p1 = B * FA, p2 = p1 * (Z + B), p3 = p2 * Z;
+    const double r4 = 1.0 / (p3 * FZ);
+    const double invFZ = r4 * p3, r3 = r4 * FZ;
+    const double invZ = r3 * p2, r2 = r3 * Z;
+    const double invZpB = r2 * p1, r1 = r2 * (Z + B);
+    const double invZB = r1 * B, invB = r1 * FA;
     const double cL = 2.0 * L * invB;  // 2 L / B
     const double Zm1 = Z - 1.0;
     // Zc = sum c_k Z_k, Lc = sum c_k L_k

@@ -34,10 +34,17 @@ struct WS {
     double* tm;        // [2 n]
     int32_t* tflag;    // [2 n]: ss iters | tr iters << 8 | used_tr << 16 | maxiter << 17 | nonfinite << 18
     int32_t *q_stab, *q_split, *q_stab_tr, *q_split_tr;
+    int32_t* q_sort;   // [n]: the split trust-region queue laid out longest expected runs first
     int32_t* cnt;      // queue counters and read heads (enums below)
     float* nnp = nullptr;  // learned form: classifier logits [n]
     float* nnk = nullptr;  // learned form: initializer ln K [NC n]
     Ctl ctl;               // tolerances and iteration caps of the call
+    // learned form: mixtures whose network route the plain method rejected
+    // (q_redo, count in cnt[Q_REDO]); q_pre != nullptr makes the precheck
+    // take its mixtures from that list instead of 0 .. n-1
+    int32_t* q_redo = nullptr;
+    const int32_t* q_pre = nullptr;
+    unsigned long long* acc = nullptr;  // queue sizes summed over the passes of a call
 };
 
 struct IO {
@@ -55,18 +62,41 @@ struct IO {
 // precheck (or the classifier gate), counter Q_SPLIT; from the back by the
 // stability decision, counter Q_SPLIT_B (entry k at n - 1 - k).  The two parts
 // do not depend on each other, so their split SS can run concurrently.
-enum { Q_STAB = 0, Q_SPLIT = 1, Q_STAB_TR = 2, Q_SPLIT_TR = 3, Q_SPLIT_TR_SLOW = 4, Q_SPLIT_TR_FAST = 5,
-       Q_SPLIT_B = 6 };
-// Split TR queue order: the runs whose last SS updates contracted slowly
-// (ratio above kSlowSS) are expected to need the most trust-region steps;
-// they fill the queue from the front and the others from the back, so that
-// the longest runs start first and the kernel's tail shortens.  Only the
-// order of the work changes.
+enum { Q_STAB = 0, Q_SPLIT = 1, Q_STAB_TR = 2, Q_SPLIT_TR = 3, Q_SPLIT_B = 6 };
+// Split trust-region queue order.  A trust-region run is a chain of dependent
+// evaluations, each about as long on an otherwise idle SM as on a busy one (an
+// FP64 warp instruction occupies the SM's narrow FP64 pipe as long whatever
+// the number of active lanes), so a long run that starts late sets the
+// kernel's length.  The split SS rates each hand-off by the residual it leaves
+// and its last contraction ratio -- runs that leave SS far from convergence,
+// or contracting slowly, take the most trust-region steps -- into kTRBuckets
+// buckets, and k_tr_order lays the queue out longest expected runs first.
+// Only the order of the work changes.  (The same order for the stability
+// trust region measured slower: 7.0 -> 7.4 ms at nc = 8, 1e6.)
+constexpr int kTRBuckets = 8;
+constexpr int QB_SPLIT = 32;  // cnt slots: split items per bucket, then the scatter cursors
+__device__ __forceinline__ int tr_bucket(double log10_res, bool slow, double slow_bonus) {
+    const double score = log10_res + (slow ? slow_bonus : 0.0);
+    return (int)fmin(fmax(floor(-score), 0.0), (double)(kTRBuckets - 1));
+}
+// Split SS hand-off: contraction ratio above which SS counts as slow.
 constexpr double kSlowSS = 0.3;
 // ws.tflag bit: a stability item the FP32 pre-iteration handed to the FP64 SS
 constexpr int kSSFinish = 1 << 20;
 enum { H_PRE = 8, H_STAB = 9, H_STAB_TR = 10, H_SPLIT = 11, H_SPLIT_TR = 12, H_SPLIT_B = 13, H_STAB_FIN = 14,
        H_PRE32 = 15, H_SPLIT32 = 16, H_SPLIT32_B = 17 };
+// Every slot but Q_REDO holds one pass's queue counters and read heads; the
+// learned form's second pass (over the rejected mixtures) starts them at zero
+// again.  Q_REDO counts the rejected mixtures.
+constexpr int Q_REDO = 4;
+constexpr int kCntSlots = 64;  // the counter block of a workspace
+
+// Fold one pass's four queue counters into the call's accumulator (the split
+// queue is counted from both of its ends).
+static __global__ void k_fold_counts(const int32_t* cnt, unsigned long long* acc) {
+    if (threadIdx.x < 4)
+        acc[threadIdx.x] += (unsigned long long)cnt[threadIdx.x] + (threadIdx.x == Q_SPLIT ? cnt[Q_SPLIT_B] : 0);
+}
 
 // Component data of a launch.  OneSys: one fluid system, a kernel parameter
 // read through the constant bank.  ManySys: several systems of the same nc (a
@@ -103,30 +133,6 @@ __device__ __forceinline__ void warp_append_back(int32_t* cnt, int32_t* queue, i
     if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (pred) queue[cap - 1 - (base + __popc(m & ((1u << lane) - 1u)))] = value;
-}
-
-// Append to a queue of capacity cap filled from both ends: slow = true at
-// the front (counter *cs), else at the back (counter *cb, entry k at
-// cap - 1 - k); *ct counts both.  Every lane of the warp must call it.
-__device__ __forceinline__ void warp_append2(int32_t* ct, int32_t* cs, int32_t* cb, int32_t* queue, int64_t cap,
-                                             bool pred, bool slow, int32_t value) {
-    const unsigned m = __ballot_sync(0xffffffffu, pred);
-    if (!m) return;
-    const unsigned ms = __ballot_sync(0xffffffffu, pred && slow), mb = m & ~ms;
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    int bs = 0, bb = 0;
-    if (lane == 0) {
-        atomicAdd(ct, __popc(m));
-        if (ms) bs = atomicAdd(cs, __popc(ms));
-        if (mb) bb = atomicAdd(cb, __popc(mb));
-    }
-    bs = __shfl_sync(0xffffffffu, bs, 0);
-    bb = __shfl_sync(0xffffffffu, bb, 0);
-    if (pred) {
-        if (slow) queue[bs + __popc(ms & lt)] = value;
-        else queue[cap - 1 - (bb + __popc(mb & lt))] = value;
-    }
 }
 
 // Refill for persistent kernels: the lanes that need work (need = true) take
@@ -279,6 +285,13 @@ __global__ void __launch_bounds__(128) k_prep(const __grid_constant__ CS cs, WS 
 // stability analysis.  Returns +1 root in (0, 1), -1 stability analysis, 0
 // within the relative margin `rel` of either sign test.
 // ---------------------------------------------------------------------------
+// The precheck sends a mixture to stability analysis: the plain route from
+// there on (a mixture the classifier called unstable loses its network bits;
+// the reject bit of a second-pass mixture stays).
+__device__ __forceinline__ void route_to_stability(const IO& io, int64_t m) {
+    io.status[m] = (io.status[m] & ST_NN_REJECT) | ST_STAB_RUN;
+}
+
 template <int NC, class F>
 __device__ __forceinline__ int rr_route(const F* z, const F* K, F rel) {
     F f0 = 0, f1 = 0, s0 = 0, s1 = 0;
@@ -347,7 +360,7 @@ struct PrecheckSS {
             return 0;
         }
         if (!rachford_rice<NC>(z, K, th, t) || !(th > 0.0 && th < 1.0)) {
-            io.status[m] = ST_STAB_RUN;
+            route_to_stability(io, m);
             return 1;
         }
 #pragma unroll
@@ -386,12 +399,16 @@ struct PrecheckSS {
             }
         }
         if (!(tx < -kEpsNeg || ty < -kEpsNeg || dG < -kEpsNeg)) {
-            io.status[m] = ST_STAB_RUN;
+            route_to_stability(io, m);
             return 1;
         }
-        io.status[m] = ST_PRECHECK_UNSTABLE;
+        io.status[m] |= ST_PRECHECK_UNSTABLE;
+        // the split starts from the precheck's K, or from the initializer's
+        // (learned form) for a mixture the classifier called unstable
+        const bool net = (io.status[m] & ST_NN_INIT) != 0;
 #pragma unroll
-        for (int i = 0; i < NC; i++) ws.lnK[i * n + m] = lnK[i];
+        for (int i = 0; i < NC; i++)
+            ws.lnK[i * n + m] = net ? fmin(fmax((double)ws.nnk[i * n + m], -15.0), 15.0) : lnK[i];
         return 2;
     }
 };
@@ -442,7 +459,7 @@ struct PrecheckSS32 {
             return 3;
         }
         if (route < 0) {
-            io.status[m] = ST_STAB_RUN;
+            route_to_stability(io, m);
             return 1;
         }
         if (!rachford_rice_f<NC>(z, K, th, t) || !(th > 0.0f && th < 1.0f)) {  // rounding at a clear margin
@@ -471,15 +488,29 @@ struct PrecheckSS32 {
     }
 };
 
+// Mixtures the precheck takes: 0 .. n-1, or the list ws.q_pre (learned form,
+// second pass).  Only those not yet routed run it (status 0, or only the
+// learned form's bits: unstable by the classifier, or rejected by the judge):
+// the others are final (non-finite, stable by the classifier) or routed.
+constexpr int kPrecheckBits = ST_NN_REJECT | ST_NN_UNSTABLE | ST_NN_INIT;
+__device__ __forceinline__ int64_t precheck_len(const WS& ws) {
+    return ws.q_pre ? (int64_t)(*(volatile int32_t*)(ws.cnt + Q_REDO)) : ws.n;
+}
+__device__ __forceinline__ int64_t precheck_item(const WS& ws, const IO& io, int64_t pos) {
+    if (pos < 0) return -1;
+    const int64_t m = ws.q_pre ? (int64_t)ws.q_pre[pos] : pos;
+    return (io.status[m] & ~kPrecheckBits) == 0 ? m : -1;
+}
+
 template <int NC, class CS>
 __global__ void __launch_bounds__(128) k_precheck32(const __grid_constant__ CS cs, WS ws, IO io) {
-    const int64_t len = ws.n;
+    const int64_t len = precheck_len(ws);
     PrecheckSS32<NC> s;
     bool have = false, drained = false;
     for (;;) {
-        const int64_t pos = warp_fetch(ws.cnt + H_PRE32, !have, len, drained);
-        if (pos >= 0 && !(io.status[pos] & ST_NONFINITE)) {
-            s.begin(cs, ws, io, pos);
+        const int64_t m = precheck_item(ws, io, warp_fetch(ws.cnt + H_PRE32, !have, len, drained));
+        if (m >= 0) {
+            s.begin(cs, ws, io, m);
             have = true;
         }
         if (!__any_sync(0xffffffffu, have) && drained) break;
@@ -497,18 +528,15 @@ __global__ void __launch_bounds__(128) k_precheck32(const __grid_constant__ CS c
 // no faster that way).
 template <int NC, class CS>
 __global__ void __launch_bounds__(128, 3) k_precheck(const __grid_constant__ CS cs, WS ws, IO io) {
-    const int64_t len = ws.n;
+    const int64_t len = precheck_len(ws);
     PrecheckSS<NC> s;
     bool have = false, drained = false;
     for (;;) {
-        const int64_t pos = warp_fetch(ws.cnt + H_PRE, !have, len, drained);
-        if (pos >= 0) {
-            if (io.status[pos] != 0) {
-                // final, or sent to stability analysis already; this lane fetches again next round
-            } else {
-                s.begin_finish(cs, ws, io, pos);
-                have = true;
-            }
+        // a mixture that is final or routed already is skipped: the lane fetches again next round
+        const int64_t m = precheck_item(ws, io, warp_fetch(ws.cnt + H_PRE, !have, len, drained));
+        if (m >= 0) {
+            s.begin_finish(cs, ws, io, m);
+            have = true;
         }
         if (!__any_sync(0xffffffffu, have) && drained) break;
         const int r = have ? s.step(cs, ws, io) : 0;
@@ -676,12 +704,7 @@ struct StabSS32 {
         const Comp<NC>& cp = cs.of(m);
         t = (int)(item & 1);
         double lnKw[NC];
-        if (io.status[m] & ST_NN_INIT) {
-#pragma unroll
-            for (int i = 0; i < NC; i++) lnKw[i] = ws.lnK[i * n + m];
-        } else {
-            wilson<NC>(cp, io.P[m], io.T[m], lnKw);
-        }
+        wilson<NC>(cp, io.P[m], io.T[m], lnKw);
 #pragma unroll
         for (int i = 0; i < NC; i++) {
             sA[i] = (float)ws.sA[i * n + m];
@@ -812,24 +835,43 @@ struct StabPt {
     double H[NC * (NC + 1) / 2];
 };
 
+// sWin (optional): sqrt(W_i) of the point, when the caller has it (a trust-
+// region trial point beta + u gives it without an exponential); else from
+// ln W.  W = sqrt(W)^2, so no square root is taken either way.
 template <int NC>
-__device__ __forceinline__ bool stab_point(const Comp<NC>& cp, const Mix<NC>& mx, const double* d, StabPt<NC>& p) {
-    double W[NC], c[NC], Wt;
-    Phase<NC> ph;
-    if (!stab_eval<NC>(cp, mx, d, p.lnW, W, Wt, c, ph, p.gt, p.tm)) return false;
-    double J[NC * (NC + 1) / 2];
-    dlnphi_dn<NC>(cp, mx, c, ph, J);
-    double sW[NC], inv = 1.0 / Wt;
+__device__ __forceinline__ bool stab_point(const Comp<NC>& cp, const Mix<NC>& mx, const double* d, StabPt<NC>& p,
+                                           const double* sWin = nullptr) {
+    double sW[NC], W[NC], c[NC], Wt = 0.0;
 #pragma unroll
     for (int i = 0; i < NC; i++) {
-        sW[i] = sqrt(W[i]);
-        p.g[i] = sW[i] * p.gt[i];
+        sW[i] = sWin ? sWin[i] : exp_fast(0.5 * p.lnW[i]);
+        W[i] = sW[i] * sW[i];
+        Wt += W[i];
     }
+    const double inv = 1.0 / Wt;
 #pragma unroll
-    for (int i = 0; i < NC; i++)
+    for (int i = 0; i < NC; i++) c[i] = W[i] * inv;
+    Phase<NC> ph;
+    eos<NC>(cp, mx, c, ph);
+    double t = 1.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        p.gt[i] = p.lnW[i] + ph.lnphi[i] - d[i];
+        t = fma(W[i], p.gt[i] - 1.0, t);
+    }
+    p.tm = t;
+    if (!isfinite(t)) return false;
+    double J[NC * (NC + 1) / 2];
+    dlnphi_dn<NC>(cp, mx, c, ph, J);
+#pragma unroll
+    for (int i = 0; i < NC; i++) p.g[i] = sW[i] * p.gt[i];
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        const double ri = sW[i] * inv;
 #pragma unroll
         for (int j = 0; j <= i; j++)
-            p.H[tri(i, j)] = sW[i] * sW[j] * J[tri(i, j)] * inv + (i == j ? 1.0 + 0.5 * p.gt[i] : 0.0);
+            p.H[tri(i, j)] = ri * sW[j] * J[tri(i, j)] + (i == j ? 1.0 + 0.5 * p.gt[i] : 0.0);
+    }
     return true;
 }
 
@@ -881,7 +923,7 @@ struct StabTR {
     __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io, bool tail) {
         const Comp<NC>& cp = cs.of(m);
         StabPt<NC> nxt;
-        double u[NC], pred = 0.0;
+        double u[NC], sWn[NC], pred = 0.0;
         if (phase == 0) {
 #pragma unroll
             for (int i = 0; i < NC; i++) nxt.lnW[i] = cur.lnW[i];
@@ -902,9 +944,12 @@ struct StabTR {
                 pred = fma(cur.g[i], u[i], fma(0.5 * u[i], hd, pred));
             }
 #pragma unroll
-            for (int i = 0; i < NC; i++) nxt.lnW[i] = 2.0 * log_fast(0.5 * fabs(beta[i] + u[i]));
+            for (int i = 0; i < NC; i++) {
+                sWn[i] = 0.5 * fabs(beta[i] + u[i]);
+                nxt.lnW[i] = 2.0 * log_fast(sWn[i]);
+            }
         }
-        const bool ok = stab_point<NC>(cp, mx, d, nxt);
+        const bool ok = stab_point<NC>(cp, mx, d, nxt, phase == 0 ? nullptr : sWn);
         if (phase == 0) {
             if (!ok) {
                 store(ws, 0, 1);
@@ -1039,7 +1084,7 @@ struct SplitSS {
     int64_t m;
     Mix<NC> mx;
     double z[NC], lnK[NC], dp[NC], dem_f, res_prev, th;
-    int it, iters;
+    int it, iters, bucket;
     bool dem_pending, slow_hint;
 
     template <class CS>
@@ -1081,8 +1126,7 @@ struct SplitSS {
         if (io.iters) io.iters[m] = (io.iters[m] & ~0xff) | (iters & 0xff);
     }
 
-    // 0 continue, 1 done, 2 needs the trust region, 3 needs it and converged
-    // slowly in SS
+    // 0 continue, 1 done, 2 needs the trust region (order bucket in `bucket`)
     template <class CS>
     __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io) {
         const Comp<NC>& cp = cs.of(m);
@@ -1147,7 +1191,11 @@ struct SplitSS {
                 ws.nV[i * n + m] = inside ? th * y[i] : 0.5 * K[i] * z[i] / (1.0 + 0.5 * (K[i] - 1.0));
             finish(io, ST_SPLIT_TR);
             const double dpm = maxabs<NC>(dp);  // 0 when this iteration took no update yet
-            return (dpm > 0.0 ? res > kSlowSS * dpm : slow_hint) ? 3 : 2;
+            const bool slow = dpm > 0.0 ? res > kSlowSS * dpm : slow_hint;
+            // expected length: about one more trust-region step per decade of
+            // residual, and several more when SS contracted slowly
+            bucket = tr_bucket(log_fast(res) * 0.4342944819032518, slow, 3.0);
+            return 2;
         }
         double dk[NC];
 #pragma unroll
@@ -1345,8 +1393,11 @@ __global__ void __launch_bounds__(128, 3) k_split_ss(const __grid_constant__ CS 
         }
         if (!__any_sync(0xffffffffu, have)) break;
         const int r = have ? s.step(cs, ws, io) : 0;
-        warp_append2(ws.cnt + Q_SPLIT_TR, ws.cnt + Q_SPLIT_TR_SLOW, ws.cnt + Q_SPLIT_TR_FAST, ws.q_split_tr, ws.n,
-                     r >= 2, r == 3, (int32_t)s.m);
+        warp_append(ws.cnt + Q_SPLIT_TR, ws.q_split_tr, r == 2, (int32_t)s.m);
+        if (r == 2) {
+            ws.tflag[s.m] = s.bucket;
+            atomicAdd(ws.cnt + QB_SPLIT + s.bucket, 1);
+        }
         if (r) have = false;
     }
 }
@@ -1362,13 +1413,15 @@ struct SplitPt {
 };
 
 template <int NC>
-__device__ __forceinline__ bool split_point(const Comp<NC>& cp, const Mix<NC>& mx, const double* z, const double* nV,
-                                            SplitPt<NC>& p) {
+__device__ __forceinline__ bool split_point(const Comp<NC>& cp, const Mix<NC>& mx, const double* z, const double* iz,
+                                            const double* nV, SplitPt<NC>& p) {
     double th = 0.0;
 #pragma unroll
     for (int i = 0; i < NC; i++) th += nV[i];
     p.th = th;
-    const double iv = 1.0 / th, il = 1.0 / (1.0 - th);
+    // one division: w = 1 / (theta (1 - theta)), 1 / theta = w (1 - theta), 1 / (1 - theta) = w theta
+    const double w = 1.0 / (th * (1.0 - th));
+    const double iv = w * (1.0 - th), il = w * th;
 #pragma unroll
     for (int i = 0; i < NC; i++) {
         p.y[i] = nV[i] * iv;
@@ -1390,34 +1443,40 @@ __device__ __forceinline__ bool split_point(const Comp<NC>& cp, const Mix<NC>& m
         G = fma(z[i] - nV[i], mul, fma(nV[i], muv, G));
     }
     p.G = G;
-    const double w = 1.0 / (th * (1.0 - th));
+    // scaling S_i = (z_i / (x_i y_i))^(-1/2) of u = D^(1/2) dn^V; the diagonal
+    // term z_i / (x_i y_i) of the Hessian then scales to exactly 1
 #pragma unroll
     for (int i = 0; i < NC; i++) {
-        double md = z[i] / (p.x[i] * p.y[i]);
-        p.S[i] = 1.0 / sqrt(md);
+        p.S[i] = sqrt(p.x[i] * p.y[i] * iz[i]);
         p.gs[i] = p.S[i] * p.gt[i];
     }
 #pragma unroll
-    for (int i = 0; i < NC; i++)
+    for (int i = 0; i < NC; i++) {
+        const double wSi = w * p.S[i];
 #pragma unroll
         for (int j = 0; j <= i; j++) {
-            double h = th * JL[tri(i, j)] + (1.0 - th) * JV[tri(i, j)] - 1.0;
-            if (i == j) h += z[i] / (p.x[i] * p.y[i]);
-            p.Hs[tri(i, j)] = w * h * p.S[i] * p.S[j];
+            const double h = th * JL[tri(i, j)] + (1.0 - th) * JV[tri(i, j)] - 1.0;
+            p.Hs[tri(i, j)] = (i == j) ? fma(wSi * p.S[i], h, w) : wSi * p.S[j] * h;
         }
+    }
     return isfinite(G);
 }
 
-// 0.99 fraction-to-boundary cut keeping 0 < n^V_i + d_i < z_i
+// 0.99 fraction-to-boundary cut keeping 0 < n^V_i + d_i < z_i: the smallest
+// ratio is found by cross-multiplication, with one division at the end
 template <int NC>
 __device__ __forceinline__ double boundary_cut(const double* z, const double* nV, const double* d) {
-    double tau = 1.0;
+    double num = 1.0, den = 1.0;  // tau = num / den, starting at 1
 #pragma unroll
     for (int i = 0; i < NC; i++) {
-        if (d[i] < 0.0) tau = fmin(tau, 0.99 * nV[i] / (-d[i]));
-        else if (d[i] > 0.0) tau = fmin(tau, 0.99 * (z[i] - nV[i]) / d[i]);
+        const double a = d[i] < 0.0 ? 0.99 * nV[i] : 0.99 * (z[i] - nV[i]);
+        const double b = fabs(d[i]);
+        if (b > 0.0 && a * den < num * b) {
+            num = a;
+            den = b;
+        }
     }
-    return tau;
+    return num == den ? 1.0 : num / den;
 }
 
 // One step = one factorisation of the subproblem and, once its step is known,
@@ -1431,7 +1490,7 @@ struct SplitTR {
     int it, iters, newton_steps, phase;  // phase 0: start point; 1: trust region; 2: Newton polish
     int32_t st;
     Mix<NC> mx;
-    double z[NC], nV[NC], radius, eta_lo;
+    double z[NC], iz[NC], nV[NC], radius, eta_lo;  // iz = 1 / z
     TRShift sh;
     SplitPt<NC> cur;
 
@@ -1444,6 +1503,7 @@ struct SplitTR {
 #pragma unroll
         for (int i = 0; i < NC; i++) {
             z[i] = io.z[i * io.ld + m];
+            iz[i] = 1.0 / z[i];
             nV[i] = ws.nV[i * n + m];
         }
         st = io.status[m];
@@ -1510,7 +1570,7 @@ struct SplitTR {
             for (int i = 0; i < NC; i++) trial[i] = nV[i] + dstep[i];
         }
         SplitPt<NC> nxt;
-        const bool ok = split_point<NC>(cp, mx, z, trial, nxt);
+        const bool ok = split_point<NC>(cp, mx, z, iz, trial, nxt);
         if (phase == 0) {
             if (!ok) return finish(io, 1);
             cur = nxt;
@@ -1545,7 +1605,9 @@ struct SplitTR {
                 st |= ST_MAXITER;
                 return finish(io, 0);
             }
-        } else if (it >= ws.ctl.tr_split) {
+        } else if (it >= ((st & ST_NN_INIT) ? min(ws.ctl.tr_split, kTRStab) : ws.ctl.tr_split)) {
+            // a network-started run gets the paper's stability cap K_tr (Alg. 2):
+            // one that has not converged by then is redone by the plain method
             st |= ST_MAXITER;
             return finish(io, 0);
         }
@@ -1553,16 +1615,36 @@ struct SplitTR {
     }
 };
 
+// Lay the split trust-region queue out by bucket (longest expected runs
+// first) into ws.q_sort: each block forms the bucket offsets from the counts,
+// and the items of a bucket take consecutive positions from its cursor.
+static __global__ void __launch_bounds__(128) k_tr_order(WS ws) {
+    __shared__ int base[kTRBuckets];
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int b = 0; b < kTRBuckets; b++) {
+            base[b] = acc;
+            acc += *(volatile int32_t*)(ws.cnt + QB_SPLIT + b);
+        }
+    }
+    __syncthreads();
+    const int64_t len = *(volatile int32_t*)(ws.cnt + Q_SPLIT_TR);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < len; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t m = ws.q_split_tr[k];
+        const int b = ws.tflag[m];
+        ws.q_sort[base[b] + atomicAdd(ws.cnt + QB_SPLIT + kTRBuckets + b, 1)] = m;
+    }
+}
+
 template <int NC, class CS>
 __global__ void __launch_bounds__(128, 3) k_split_tr(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_SPLIT_TR);
-    const int64_t slow = *(volatile int32_t*)(ws.cnt + Q_SPLIT_TR_SLOW);
     SplitTR<NC> s;
     bool have = false, drained = false;
     for (;;) {
         const int64_t pos = warp_fetch(ws.cnt + H_SPLIT_TR, !have, len, drained);
         if (pos >= 0) {
-            s.begin(cs, ws, io, ws.q_split_tr[pos < slow ? pos : ws.n - 1 - (pos - slow)]);
+            s.begin(cs, ws, io, ws.q_sort[pos]);  // in the order k_tr_order laid out
             have = true;
         }
         if (!__any_sync(0xffffffffu, have)) break;
@@ -1629,19 +1711,51 @@ __global__ void __launch_bounds__(128) k_phase_eos(const __grid_constant__ Comp<
 }
 
 // ---------------------------------------------------------------------------
-// Learned form (Sec. 4.3): gate each mixture on the classifier's probability
-// p of being stable.  p >= p_r: single phase; p <= p_l: phase split from the
-// initializer's ln K (if finite and bracketing K = 1); otherwise stability
-// analysis with trials initialised from the initializer's K (Wilson K when
-// the initializer output is not finite).  ln K is clamped to [-15, 15].
+// Learned form (Sec. 4.3), with the plain method as judge of what the networks
+// decide.  The classifier gives the probability p that the mixture is stable:
+//  - p >= p_r: single phase (NN_STABLE), unless tpd (Eq. tpd) is negative at
+//    one of four trial phases, w proportional to z K and to z / K for the
+//    initializer's K and for Wilson K (the trials of Sec. 2.2.1, before any
+//    iteration).  A negative tpd proves instability: such a mixture takes the
+//    plain route instead.
+//  - p <= p_l with the initializer's ln K finite and bracketing K = 1
+//    (NN_UNSTABLE | NN_INIT): the plain precheck still runs, and only if it
+//    proves instability does the split start from the initializer's K (else
+//    the mixture takes the plain route from stability analysis on: where the
+//    precheck cannot prove instability, the plain method's split starts from
+//    a stability trial, and near three-phase conditions the initializer's K
+//    can lead to another stationary point of G).  k_nn_judge checks the split.
+//  - otherwise the plain route (status 0): the precheck, stability analysis
+//    from Wilson K and the split, exactly as in the plain flash.
+// The initializer's ln K are clamped to [-15, 15].
 // ---------------------------------------------------------------------------
+template <int NC>
+__device__ __forceinline__ double trial_tpd(const Comp<NC>& cp, const Mix<NC>& mx, const double* z, const double* d,
+                                            const double* lnK, bool vapour_like) {
+    double w[NC], sw = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        w[i] = z[i] * exp_fast(vapour_like ? lnK[i] : -lnK[i]);
+        sw += w[i];
+    }
+    const double inv = 1.0 / sw;
+#pragma unroll
+    for (int i = 0; i < NC; i++) w[i] *= inv;
+    Phase<NC> ph;
+    eos<NC>(cp, mx, w, ph);
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; i++) t = fma(w[i], log_fast(w[i]) + ph.lnphi[i] - d[i], t);
+    return t;  // NaN when not finite: no proof either way
+}
+
 template <int NC, class CS>
 __global__ void __launch_bounds__(128) k_nn_route(const __grid_constant__ CS cs, WS ws, IO io, float p_l,
                                                   float p_r) {
     const int64_t n = ws.n;
     PTF_WARP_ROUNDS(n, m, valid) {
-        int route = 0;
         if (valid && !(io.status[m] & ST_NONFINITE)) {
+            const Comp<NC>& cp = cs.of(m);
             const float p = 1.0f / (1.0f + __expf(-ws.nnp[m]));
             double lnK[NC], kmax = -1e300, kmin = 1e300;
             bool fin = true;
@@ -1655,27 +1769,83 @@ __global__ void __launch_bounds__(128) k_nn_route(const __grid_constant__ CS cs,
                 kmin = fmin(kmin, v);
             }
             if (p >= p_r) {
-                double z[NC];
+                double z[NC], d[NC], lw[NC];
+                Mix<NC> mx;
+                load_mix<NC>(ws, m, mx);
+                wilson<NC>(cp, io.P[m], io.T[m], lw);
 #pragma unroll
-                for (int i = 0; i < NC; i++) z[i] = io.z[i * io.ld + m];
-                io.status[m] = ST_NN_STABLE;
-                write_single<NC>(io, m, z);
-            } else {
-                if (fin) {
-#pragma unroll
-                    for (int i = 0; i < NC; i++) ws.lnK[i * n + m] = lnK[i];
+                for (int i = 0; i < NC; i++) {
+                    z[i] = io.z[i * io.ld + m];
+                    d[i] = ws.d[i * n + m];
+                    lw[i] = fmin(fmax(lw[i], -30.0), 30.0);
                 }
-                if (p <= p_l && fin && kmax > 0.0 && kmin < 0.0) {
-                    io.status[m] = ST_NN_UNSTABLE | ST_NN_INIT;
-                    route = 2;
+                bool unstable = false;
+#pragma unroll 1
+                for (int t = fin ? 0 : 2; t < 4 && !unstable; t++)
+                    unstable = trial_tpd<NC>(cp, mx, z, d, t < 2 ? lnK : lw, (t & 1) == 0) < -kEpsNeg;
+                if (unstable) {
+                    io.status[m] = 0;  // the plain route
                 } else {
-                    io.status[m] = ST_STAB_RUN | (fin ? ST_NN_INIT : 0);
-                    route = 1;
+                    io.status[m] = ST_NN_STABLE;
+                    write_single<NC>(io, m, z);
                 }
+            } else if (p <= p_l && fin && kmax > 0.0 && kmin < 0.0) {
+                io.status[m] = ST_NN_UNSTABLE | ST_NN_INIT;  // the precheck decides the split's start
+            } else {
+                io.status[m] = 0;  // the plain route
             }
         }
-        warp_append(ws.cnt + Q_STAB, ws.q_stab, route == 1, (int32_t)m);
-        warp_append(ws.cnt + Q_SPLIT, ws.q_split, route == 2, (int32_t)m);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Judge of the network-started splits (learned form, Sec. 4.3): a mixture the
+// classifier and the precheck sent to the split from the initializer's K keeps
+// that result only if the split proves instability where the initializer
+// pointed: two phases, converged
+// (no cap, no collapse, finite), Delta G = sum z_i (mu_i - d_i) < -1e-10 at
+// the converged phases (mu_i = ln x_i + ln phi_i(x), the same in both phases;
+// d_i = ln z_i + ln phi_i(z)), and every converged ln K_i within
+// ctl.nn_lnk_dev of the network's.  Any other outcome -- one phase, a cap, a
+// non-finite state, or a stationary point of G far from the prediction (where
+// several exist the plain method can reach another) -- is redone by the plain
+// method: status NN_REJECT, appended to q_redo for the second pass.
+// ---------------------------------------------------------------------------
+template <int NC, class CS>
+__global__ void __launch_bounds__(128) k_nn_judge(const __grid_constant__ CS cs, WS ws, IO io) {
+    const int64_t len = *(volatile int32_t*)(ws.cnt + Q_SPLIT);  // the front part of the split queue
+    const int64_t n = ws.n;
+    PTF_WARP_ROUNDS(len, qi, valid) {
+        const int64_t m = valid ? ws.q_split[qi] : 0;
+        bool redo = false;
+        if (valid && (io.status[m] & ST_NN_UNSTABLE)) {
+            const int32_t st = io.status[m];
+            redo = io.nphase[m] != 2 || (st & (ST_MAXITER | ST_COLLAPSE | ST_NONFINITE)) != 0;
+            if (!redo) {
+                const Comp<NC>& cp = cs.of(m);
+                double x[NC], z[NC], dev = 0.0;
+                Mix<NC> mx;
+                load_mix<NC>(ws, m, mx);
+#pragma unroll
+                for (int i = 0; i < NC; i++) {
+                    x[i] = io.x[i * io.ld + m];
+                    z[i] = io.z[i * io.ld + m];
+                    const double net = fmin(fmax((double)ws.nnk[i * n + m], -15.0), 15.0);
+                    dev = fmax(dev, fabs(log_fast(io.K[i * io.ld + m]) - net));
+                }
+                Phase<NC> px;
+                eos<NC>(cp, mx, x, px);
+                double dG = 0.0;
+#pragma unroll
+                for (int i = 0; i < NC; i++) dG = fma(z[i], log_fast(x[i]) + px.lnphi[i] - ws.d[i * n + m], dG);
+                redo = !(dG < -kEpsNeg) || !(dev <= ws.ctl.nn_lnk_dev);
+            }
+            if (redo) {
+                io.status[m] = ST_NN_REJECT;
+                if (io.iters) io.iters[m] = 0;
+            }
+        }
+        warp_append(ws.cnt + Q_REDO, ws.q_redo, redo, (int32_t)m);
     }
 }
 

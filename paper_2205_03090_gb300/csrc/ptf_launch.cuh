@@ -49,7 +49,9 @@ constexpr int kFillerQuota = 256;
 
 // The flash pipeline over one workspace.  mode 0: plain flash; mode 1:
 // stability only; mode 2: learned form (nn = {classifier, initializer}, p_l /
-// p_r its thresholds).  ev (optional, kStages + 1 events) is recorded before
+// p_r its thresholds; the plain method judges the networks' routes, and a
+// second pass of the plain stages redoes the rejected mixtures, the split
+// trust-region stage's events then covering both).  ev (optional, kStages + 1 events) is recorded before
 // each stage and after the last one.  `grid` is the grid of the one-pass
 // kernels; the persistent kernels are sized to the device (sms = grid / 8),
 // or to `pgrid` blocks when it is positive.  CS is the component source
@@ -91,6 +93,9 @@ cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, 
         if (e == cudaSuccess) e = nn_infer_launch(nn[1], NC, ws.n, io.ld, io.P, io.T, io.z, ws.nnk, ws.n, sms, s);
         if (e != cudaSuccess) return e;
         k_nn_route<NC, CS><<<grid, 128, 0, s>>>(cs, ws, io, p_l, p_r);
+        // the mixtures the networks leave to the plain method (status 0)
+        k_precheck32<NC, CS><<<pg(g_p32), 128, 0, s>>>(cs, ws, io);
+        k_precheck<NC, CS><<<pg(g_pre), 128, 0, s>>>(cs, ws, io);
     } else {
         k_prep<NC, false, CS><<<grid, 128, 0, s>>>(cs, ws, io);
     }
@@ -116,7 +121,28 @@ cudaError_t launch_pipeline(const CS& cs, const WS& ws, const IO& io, int grid, 
         k_split_ss<NC, CS><<<pg(g_sps), 128, 0, s>>>(cs, ws, io, conc ? 1 : 2, 0);
         if (conc) cudaStreamWaitEvent(s, cc->lo_done, 0);
         mark(5);
+        k_tr_order<<<grid, 128, 0, s>>>(ws);
         k_split_tr<NC, CS><<<pg(g_spt), 128, 0, s>>>(cs, ws, io);
+        if (mode == 2) {
+            // judge the network-started splits, then the plain method's second
+            // pass over the rejected mixtures (one after another, on s)
+            k_nn_judge<NC, CS><<<grid, 128, 0, s>>>(cs, ws, io);
+            if (ws.acc) k_fold_counts<<<1, 32, 0, s>>>(ws.cnt, ws.acc);
+            cudaMemsetAsync(ws.cnt, 0, Q_REDO * sizeof(int32_t), s);
+            cudaMemsetAsync(ws.cnt + Q_REDO + 1, 0, (kCntSlots - Q_REDO - 1) * sizeof(int32_t), s);
+            WS w2 = ws;
+            w2.q_pre = ws.q_redo;
+            k_precheck32<NC, CS><<<pg(g_p32), 128, 0, s>>>(cs, w2, io);
+            k_precheck<NC, CS><<<pg(g_pre), 128, 0, s>>>(cs, w2, io);
+            k_stab_ss32<NC, CS><<<pg(g_s32), 128, 0, s>>>(cs, w2, io);
+            k_stab_ss<NC, CS><<<pg(g_sss), 128, 0, s>>>(cs, w2, io);
+            k_stab_tr<NC, CS><<<pg(g_str), 128, 0, s>>>(cs, w2, io);
+            k_stab_decide<NC, CS><<<grid, 128, 0, s>>>(cs, w2, io);
+            k_split_ss32<NC, CS><<<pg(g_s3s), 128, 0, s>>>(cs, w2, io, 2, 0);
+            k_split_ss<NC, CS><<<pg(g_sps), 128, 0, s>>>(cs, w2, io, 2, 0);
+            k_tr_order<<<grid, 128, 0, s>>>(w2);
+            k_split_tr<NC, CS><<<pg(g_spt), 128, 0, s>>>(cs, w2, io);
+        }
         mark(6);
     } else {
         mark(5);

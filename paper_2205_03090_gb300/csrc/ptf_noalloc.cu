@@ -54,8 +54,8 @@ int setup(int dev, void** ptr, int* sms) {
 }
 
 // Bytes of scratch one mixture needs: (8 nc + 3) doubles of stage state and
-// 7 int32 of queue entries; 256 bytes of queue counters per call.
-size_t bytes_per_mixture(int nc) { return (size_t)(8 * nc + 3) * sizeof(double) + 7 * sizeof(int32_t); }
+// 8 int32 of queue entries; 256 bytes of queue counters per call.
+size_t bytes_per_mixture(int nc) { return (size_t)(8 * nc + 3) * sizeof(double) + 8 * sizeof(int32_t); }
 
 WS carve(unsigned char* base, int nc, int64_t n) {
     WS w;
@@ -78,6 +78,7 @@ WS carve(unsigned char* base, int nc, int64_t n) {
     w.q_split = q; q += n;
     w.q_stab_tr = q; q += 2 * n;
     w.q_split_tr = q; q += n;
+    w.q_sort = q; q += n;
     return w;
 }
 

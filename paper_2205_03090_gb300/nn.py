@@ -179,6 +179,53 @@ def train_both(fl: ptflash.Flash, cond: wl.Conditions, cfg: TrainConfig = TrainC
     return logs
 
 
+def calibrate_thresholds(fl: ptflash.Flash, cond: wl.Conditions, margin_logit: float = 1.0, log_fn=None):
+    """Thresholds p_l <= p_r of the learned form from held-out mixtures
+    (Sec. 5.2 chooses them so that no misclassification occurs), with the
+    plain GPU flash as the reference:
+
+    * p_r: above the classifier probability of every mixture that the
+      learned form with p_l = 0 and p_r = 1/2 reports stable (NN_STABLE, so
+      its tpd trials did not catch it) while the plain flash finds two phases;
+    * p_l: below the probability of every mixture that the learned form with
+      p_l = 1/2 and p_r = 1 keeps from a network-started split (NN_UNSTABLE,
+      accepted by the judge) while the plain flash disagrees (phase count, or
+      beta, x or y by more than 1e-8).
+
+    Each bound is widened by margin_logit in logit space and is at least as
+    strict as the paper's 0.02 / 0.98.  Returns a dict with p_l, p_r and the
+    fraction of the held-out mixtures the networks then decide."""
+    import torch
+    P = torch.tensor(cond.P, device="cuda")
+    T = torch.tensor(cond.T, device="cuda")
+    z = torch.tensor(cond.z, device="cuda").contiguous()
+    plain = fl.ptflash_flash(P, T, z)
+    logit = torch.empty(1, cond.n, dtype=torch.float32, device="cuda")
+    fl.ptflash_nn_infer(CLASSIFIER, P, T, z, logit)
+    hi = fl.ptflash_flash(P, T, z, use_nn=True, p_l=0.0, p_r=0.5)
+    lo = fl.ptflash_flash(P, T, z, use_nn=True, p_l=0.5, p_r=1.0)
+    torch.cuda.synchronize()
+    lg = logit[0].double().cpu().numpy()
+    pn = plain.nphase.cpu().numpy()
+    bad_r = ((hi.status.cpu().numpy() & ptflash.PTF_ST_NN_STABLE) != 0) & (pn == 2)
+    lst = lo.status.cpu().numpy()
+    kept = ((lst & ptflash.PTF_ST_NN_UNSTABLE) != 0) & ((lst & ptflash.PTF_ST_NN_REJECTED) == 0)
+    dv = torch.maximum((lo.beta - plain.beta).abs(),
+                       torch.maximum((lo.x - plain.x).abs().amax(0), (lo.y - plain.y).abs().amax(0))).cpu().numpy()
+    bad_l = kept & ((lo.nphase.cpu().numpy() != pn) | (dv > 1e-8))
+    sig = lambda v: float(1.0 / (1.0 + np.exp(-v)))
+    p_r = max(0.98, sig(lg[bad_r].max() + margin_logit)) if bad_r.any() else 0.98
+    p_l = min(0.02, sig(lg[bad_l].min() - margin_logit)) if bad_l.any() else 0.02
+    p = 1.0 / (1.0 + np.exp(-lg))
+    decided = float(((p >= p_r) | (p <= p_l)).mean())
+    res = {"p_l": p_l, "p_r": p_r, "held_out": int(cond.n), "margin_logit": margin_logit,
+           "errors_above_half": int(bad_r.sum()), "errors_below_half": int(bad_l.sum()),
+           "decided_frac": decided, "rejected_frac_below_half": float(((lst & ptflash.PTF_ST_NN_REJECTED) != 0).mean())}
+    if log_fn:
+        log_fn(f"calibration: {res}")
+    return res
+
+
 def init_params(din, hid, dout, seed, arch=0):
     """Seeded Glorot-uniform weights and zero biases for either architecture."""
     return wl.mlp_init(din, hid, dout, seed, arch)
@@ -202,6 +249,13 @@ def save(fl: ptflash.Flash, path: str, meta: dict | None = None):
     np.concatenate(parts).astype(np.float32).tofile(path + ".bin")
     with open(path + ".json", "w") as f:
         json.dump(header, f, indent=1)
+
+
+def thresholds(header: dict):
+    """The learned form's (p_l, p_r) stored with a checkpoint, else the
+    paper's 0.02 / 0.98."""
+    t = header.get("thresholds") or {}
+    return float(t.get("p_l", 0.02)), float(t.get("p_r", 0.98))
 
 
 def load_checkpoint(fl: ptflash.Flash, path: str):

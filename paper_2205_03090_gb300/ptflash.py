@@ -26,6 +26,7 @@ PTF_ST_NONFINITE = 64
 PTF_ST_NN_STABLE = 128
 PTF_ST_NN_UNSTABLE = 256
 PTF_ST_NN_INIT = 512
+PTF_ST_NN_REJECTED = 1024
 
 _lib = None
 _VP = ctypes.c_void_p
@@ -41,12 +42,13 @@ class ptflash_options(ctypes.Structure):
     _fields_ = [("use_nn", ctypes.c_int32), ("p_l", ctypes.c_double), ("p_r", ctypes.c_double),
                 ("max_ss_stab", ctypes.c_int32), ("max_tr_stab", ctypes.c_int32), ("max_ss_split", ctypes.c_int32),
                 ("max_tr_split", ctypes.c_int32), ("max_polish", ctypes.c_int32), ("tol_stab", ctypes.c_double),
-                ("tol_split_tr", ctypes.c_double), ("tol_fug", ctypes.c_double), ("reserved", ctypes.c_int32 * 4)]
+                ("tol_split_tr", ctypes.c_double), ("tol_fug", ctypes.c_double), ("nn_lnk_dev", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 # ptflash_options fields a caller may set through **opts (0 = default)
 OPTION_FIELDS = ("max_ss_stab", "max_tr_stab", "max_ss_split", "max_tr_split", "max_polish", "tol_stab",
-                 "tol_split_tr", "tol_fug")
+                 "tol_split_tr", "tol_fug", "nn_lnk_dev")
 
 
 def load(path: str = LIB_PATH):

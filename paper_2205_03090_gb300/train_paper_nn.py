@@ -25,6 +25,7 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_OUT = os.path.join(HERE, "weights", "c9_paper")
 TRAIN_SEED = 201  # inputs drawn apart from the benchmark's
+CALIB_SEED = 203  # held-out mixtures for the thresholds
 
 
 def main(argv=None):
@@ -33,6 +34,7 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--stage2-epochs", type=int, default=4)
     ap.add_argument("--patience", type=int, default=6)
+    ap.add_argument("--calib-n", type=int, default=500_000)
     ap.add_argument("--out", default=DEFAULT_OUT)
     args = ap.parse_args(argv)
     from . import build, nn, ptflash, workloads as wl
@@ -62,6 +64,9 @@ def main(argv=None):
                                          "test_loss": s2.test_loss, "test_mae_theta": s2.test_acc,
                                          "test_mae_lnK_sum": s2.test_mae_lnK,
                                          "test_mae_lnK_per_component": s2.test_mae_lnK / nc}
+    _, cal, _ = wl.paper_case("c9", args.calib_n, CALIB_SEED)
+    meta["thresholds"] = nn.calibrate_thresholds(fl, cal, log_fn=print)
+    meta["calib_seed"] = CALIB_SEED
     nn.save(fl, args.out, meta)
     print(json.dumps(meta))
     fl.close()

@@ -3,17 +3,22 @@
 * One training step's gradient (the project's own forward / backward
   kernels, BF16 weights and activations, FP32 sums) against the FP64
   oracle of the same network on the same BF16 features and weights.
-* A short training run on plain-method flashes reduces the loss, and the
-  gated flash (classifier + initializer, p_l = 0.02, p_r = 0.98) matches the
-  CPU oracle of the plain method -- labels exact wherever |tpd| > 1e-8 up to
-  0.2 % classifier errors, two-phase values within 1e-8 up to 0.5 % of
-  multiple-stationary-point cases -- while running stability analysis on
-  far fewer mixtures.
+* A short training run on plain-method flashes reduces the loss; with
+  thresholds calibrated on held-out mixtures (Sec. 5.2) the gated flash
+  (classifier + initializer, the plain method judging both) matches the CPU
+  oracle of the plain method at the parity bars -- labels exact wherever
+  |tpd| > 1e-8, two-phase values within 1e-8, allowances only for MAXITER
+  runs -- while running stability analysis on far fewer mixtures.
+* The committed networks (3 x 64 / 3 x 128 on the 10-component workload, the
+  paper's on the 9-component case) meet the same bars at their stored
+  thresholds; with the judge made strict every network-started split is
+  redone by the plain method and the results still meet them.
 """
 import numpy as np
 import pytest
 
 from paper_2205_03090_gb300 import workloads as wl
+from test_gpu_parity import _assert_parity, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -165,12 +170,33 @@ def test_tensor_core_inference_matches_oracle(ptf, oracle_mod, which, arch, hidd
     fl.close()
 
 
-def test_training_and_learned_flash_parity(ptf, oracle_mod):
+def _learned_parity(ptf, oracle_mod, fl, comp, cond, p_l, p_r, **opts):
+    """The learned flash of cond against the oracle's plain flash."""
     import torch
+    P, T, z = (torch.tensor(a, device="cuda") for a in (cond.P, cond.T, cond.z))
+    z = z.contiguous()
+    plain = fl.ptflash_flash(P, T, z)
+    torch.cuda.synchronize()
+    plain_counts = fl.ptflash_last_counts()
+    learned = fl.ptflash_flash(P, T, z, use_nn=True, p_l=p_l, p_r=p_r, **opts)
+    torch.cuda.synchronize()
+    nn_counts = fl.ptflash_last_counts()
+    g = {k: getattr(learned, k).cpu().numpy() for k in ("nphase", "beta", "x", "y", "status")}
+    r = compare(oracle_mod, comp, cond, g)
+    st = g["status"]
+    stats = dict(nn_stable=float(((st & 128) != 0).mean()), nn_unstable=float(((st & 256) != 0).mean()),
+                 rejected=float(((st & 1024) != 0).mean()), counts=nn_counts, plain_counts=plain_counts)
+    print({k: v for k, v in r.items() if k != "bad_idx"}, stats)
+    _assert_parity(r, max_capped_frac=1e-3, check_routes=False)
+    return r, stats
+
+
+def test_training_and_learned_flash_parity(ptf, oracle_mod):
     from paper_2205_03090_gb300 import nn
     comp = wl.pseudo_components(10, 0)
     w = wl.WORKLOADS["nc10_2phase_1e6"]
     train_cond = wl.conditions(10, 200_000, 777, w["T_range"], w["P_range"], w["alpha"])
+    cal_cond = wl.conditions(10, 200_000, 779, w["T_range"], w["P_range"], w["alpha"])
     test_cond = wl.conditions(10, 20_000, 778, w["T_range"], w["P_range"], w["alpha"])
     fl = ptf.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=1 << 18)
     cfg = nn.TrainConfig(epochs=8, patience=8)
@@ -179,68 +205,57 @@ def test_training_and_learned_flash_parity(ptf, oracle_mod):
     i = logs[nn.INITIALIZER].epochs
     assert c[-1][2] < c[0][2] and i[-1][2] < i[0][2]  # validation loss fell
     assert logs[nn.CLASSIFIER].test_acc > 0.97
-    P, T, z = (torch.tensor(a, device="cuda") for a in (test_cond.P, test_cond.T, test_cond.z))
-    z = z.contiguous()
-    plain = fl.ptflash_flash(P, T, z)
-    torch.cuda.synchronize()
-    plain_counts = fl.ptflash_last_counts()
-    learned = fl.ptflash_flash(P, T, z, use_nn=True)
-    torch.cuda.synchronize()
-    nn_counts = fl.ptflash_last_counts()
-    s = oracle_mod.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
-    o = oracle_mod.flash(s, test_cond.P, test_cond.T, test_cond.z)
-    g = {k: getattr(learned, k).cpu().numpy() for k in ("nphase", "beta", "x", "y", "status")}
-    lab = g["nphase"] != o["nphase"]
-    if lab.any():
-        tp = oracle_mod.tpd_min(s, test_cond.P[lab], test_cond.T[lab], np.ascontiguousarray(test_cond.z[:, lab]))
-        graded_bad = int((np.abs(tp) > 1e-8).sum())
-    else:
-        graded_bad = 0
-    both = (g["nphase"] == 2) & (o["nphase"] == 2)
-    db = np.abs(g["beta"] - o["beta"])[both]
-    dx = np.abs(g["x"] - o["x"]).max(0)[both]
-    print("learned: label mismatches", int(lab.sum()), "graded", graded_bad, "max dbeta", db.max(), "counts",
-          nn_counts, "plain", plain_counts)
-    # classifier errors beyond the confidence thresholds are rare; splits
-    # started from the initializer's K can reach another stationary point of
-    # G where several exist (half of them below the plain method's G), so a
-    # small fraction of two-phase values may differ after this short training
-    assert graded_bad <= 0.002 * test_cond.n
-    assert (db > 1e-8).mean() < 5e-3 and (dx > 1e-8).mean() < 5e-3
-    # the classifier skips stability analysis for most mixtures
-    assert nn_counts["stab"] < 0.2 * plain_counts["stab"]
+    thr = nn.calibrate_thresholds(fl, cal_cond)
+    print("thresholds", thr)
+    r, stats = _learned_parity(ptf, oracle_mod, fl, comp, test_cond, thr["p_l"], thr["p_r"])
+    # the networks decide most mixtures, so far fewer run stability analysis
+    assert stats["nn_stable"] + stats["nn_unstable"] > 0.5
+    assert stats["counts"]["stab"] < 0.7 * stats["plain_counts"]["stab"]
+    fl.close()
+
+
+def test_committed_networks_learned_flash_10_components(ptf, oracle_mod):
+    """The committed 10-component networks at their calibrated thresholds, on
+    mixtures drawn apart from their training and calibration sets."""
+    from paper_2205_03090_gb300 import nn, train_nn
+    comp = wl.pseudo_components(10, 0)
+    w = wl.WORKLOADS["nc10_2phase_1e7"]
+    cond = wl.conditions(10, 40_000, 4242, w["T_range"], w["P_range"], w["alpha"])
+    fl = ptf.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=1 << 16)
+    meta = nn.load_checkpoint(fl, train_nn.DEFAULT_OUT)
+    p_l, p_r = nn.thresholds(meta)
+    r, stats = _learned_parity(ptf, oracle_mod, fl, comp, cond, p_l, p_r)
+    assert stats["nn_stable"] + stats["nn_unstable"] > 0.75
+    assert stats["counts"]["stab"] < 0.5 * stats["plain_counts"]["stab"]
+    fl.close()
+
+
+def test_strict_judge_redoes_network_splits(ptf, oracle_mod):
+    """With the ln K acceptance distance made tiny the judge rejects nearly
+    every network-started split; the second pass of the plain method redoes
+    them (NN_REJECTED) and the results still meet the parity bars."""
+    from paper_2205_03090_gb300 import nn, train_nn
+    comp = wl.pseudo_components(10, 0)
+    w = wl.WORKLOADS["nc10_2phase_1e7"]
+    cond = wl.conditions(10, 20_000, 4243, w["T_range"], w["P_range"], w["alpha"])
+    fl = ptf.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=1 << 13)  # several chunks
+    meta = nn.load_checkpoint(fl, train_nn.DEFAULT_OUT)
+    p_l, p_r = nn.thresholds(meta)
+    r, stats = _learned_parity(ptf, oracle_mod, fl, comp, cond, p_l, p_r, nn_lnk_dev=1e-9)
+    assert stats["rejected"] > 0.2 and stats["rejected"] >= 0.99 * stats["nn_unstable"]
     fl.close()
 
 
 def test_paper_networks_learned_flash_9_components(ptf, oracle_mod):
     """The committed paper-architecture networks (classifier 3 x 32,
-    residual + wide initializer) on the 9-component case study: the learned
-    flash matches the plain oracle (labels graded where |tpd| > 1e-8, up to
-    0.2 % classifier errors; two-phase values within 1e-8 up to 0.5 %)."""
-    import torch
+    residual + wide initializer) on the 9-component case study at their
+    calibrated thresholds: the learned flash meets the parity bars."""
     from paper_2205_03090_gb300 import nn, train_paper_nn
     comp, cond, ft = wl.paper_case("c9", 20000, 77)
     fl = ptf.Flash(comp.Tc, comp.Pc, comp.omega, comp.kij, n_max=1 << 15)
     meta = nn.load_checkpoint(fl, train_paper_nn.DEFAULT_OUT)
     assert meta["nets"][0]["hidden"] == 32 and meta["nets"][1]["arch"] == 1
-    P, T, z = (torch.tensor(a, device="cuda") for a in (cond.P, cond.T, cond.z))
-    learned = fl.ptflash_flash(P, T, z.contiguous(), use_nn=True)
-    torch.cuda.synchronize()
-    counts = fl.ptflash_last_counts()
-    s = oracle_mod.System(comp.Tc, comp.Pc, comp.omega, comp.kij)
-    o = oracle_mod.flash(s, cond.P, cond.T, cond.z)
-    g = {k: getattr(learned, k).cpu().numpy() for k in ("nphase", "beta", "x", "y", "status")}
-    lab = g["nphase"] != o["nphase"]
-    graded_bad = 0
-    if lab.any():
-        tp = oracle_mod.tpd_min(s, cond.P[lab], cond.T[lab], np.ascontiguousarray(cond.z[:, lab]))
-        graded_bad = int((np.abs(tp) > 1e-8).sum())
-    both = (g["nphase"] == 2) & (o["nphase"] == 2)
-    db = np.abs(g["beta"] - o["beta"])[both]
-    dx = np.abs(g["x"] - o["x"]).max(0)[both]
-    decided = ((g["status"] & (128 | 256)) != 0).mean()
-    print("paper nets c9: label mismatches", int(lab.sum()), "graded", graded_bad, "decided", decided, counts)
-    assert graded_bad <= 0.002 * cond.n
-    assert (db > 1e-8).mean() < 5e-3 and (dx > 1e-8).mean() < 5e-3
-    assert decided > 0.9
+    p_l, p_r = nn.thresholds(meta)
+    r, stats = _learned_parity(ptf, oracle_mod, fl, comp, cond, p_l, p_r)
+    assert stats["nn_stable"] + stats["nn_unstable"] > 0.9
     fl.close()

@@ -92,12 +92,14 @@ def compare(oracle_mod, comp, cond, g, idx=None, fug_checks=100_000):
                 bad_idx=np.nonzero((lab_bad | val_bad | route_diff) & ~capped)[0])
 
 
-def _assert_parity(r, max_capped_frac=1e-4):
-    """No miss outside MAXITER runs, every route as the oracle's, and at most
-    a fraction max_capped_frac of the mixtures stopped at a cap."""
+def _assert_parity(r, max_capped_frac=1e-4, check_routes=True):
+    """No miss outside MAXITER runs, every route as the oracle's (the plain
+    form), and at most a fraction max_capped_frac of the mixtures stopped at
+    a cap."""
     assert r["label_bad"] == 0, r
     assert r["val_bad"] == 0, r
-    assert r["route_diff"] == 0, r
+    if check_routes:
+        assert r["route_diff"] == 0, r
     assert r["capped"] <= max_capped_frac * r["n"], r
     assert r["mass_balance"] < 1e-12, r
     assert r["max_fug"] <= TOL_FUG, r
