@@ -375,9 +375,13 @@ __device__ __forceinline__ void eos(const Comp<NC>& cp, const Mix<NC>& mx, const
 // the cubic with c_k independent gives f_ik; J_ij = f_ij - sum_k c_k f_ik,
 // where the row sums reduce to closed forms (e_i is homogeneous of degree 0).
 // ---------------------------------------------------------------------------
-template <int NC>
-__device__ __forceinline__ void dlnphi_dn(const Comp<NC>& cp, const Mix<NC>& mx, const double* c, const Phase<NC>& ph,
-                                          double* J) {
+//
+// R is the type of the per-component vectors and of J.  R = float gives the
+// trust regions' model (the Hessians only shape the steps; every point the
+// steps reach is evaluated, and every decision taken, in FP64): the scalar
+// prelude, where Z - B and the derivative of the cubic can cancel, stays FP64.
+template <int NC, class R>
+__device__ __forceinline__ void dlnphi_dn_r(const Comp<NC>& cp, const Mix<NC>& mx, const Phase<NC>& ph, R* J) {
     const double A = ph.A, B = ph.B, Z = ph.Z, L = ph.L;
     const double FZ = fma(fma(3.0, Z, -2.0), Z, A - B - B * B);
     const double FA = Z - B, FB = -Z - 2.0 * B * Z - A;
@@ -394,31 +398,45 @@ __device__ __forceinline__ void dlnphi_dn(const Comp<NC>& cp, const Mix<NC>& mx,
     // Zc = sum c_k Z_k, Lc = sum c_k L_k
     const double Zc = -(FA * 2.0 * A + FB * B) * invFZ;
     const double Lc = (Zc + B) * invZpB - Zc * invZ;
+    const double qc = (Zc - B) * invZB;
     // f_ij = bb_i p_j + q_j + psi_i w_j + e_i L_j - cL Ahat_ij with
     //   p_j = Z_j - bb_j (Z - 1) + cL (psi_j - A bb_j), q_j = -(Z_j - B_j)/(Z - B),
     //   w_j = cL bb_j; the row sum of c_k f_ik is s_i (closed form).
-    double bb[NC], p[NC], q[NC], w[NC], e[NC], Lk[NC], sAc[NC];
+    const R fa2 = (R)(2.0 * FA * invFZ), fb = (R)(FB * invFZ), izpb = (R)invZpB, iz = (R)invZ, ib = (R)invB,
+            izb = (R)invZB, a = (R)A, zm1 = (R)Zm1, cl = (R)cL, zcm = (R)(Zc - Zm1), lc = (R)Lc, qcr = (R)qc;
+    R bb[NC], p[NC], q[NC], w[NC], e[NC], Lk[NC], sAc[NC], sA[NC], psi[NC], si[NC];
 #pragma unroll
     for (int k = 0; k < NC; k++) {
-        const double Zk = -(FA * 2.0 * ph.psi[k] + FB * mx.B[k]) * invFZ;
-        Lk[k] = (Zk + mx.B[k]) * invZpB - Zk * invZ;
-        bb[k] = mx.B[k] * invB;
-        e[k] = (A * bb[k] - 2.0 * ph.psi[k]) * invB;
-        p[k] = Zk - bb[k] * Zm1 + cL * (ph.psi[k] - A * bb[k]);
-        q[k] = -(Zk - mx.B[k]) * invZB;
-        w[k] = cL * bb[k];
-        sAc[k] = cL * mx.sA[k];
+        const R Bk = (R)mx.B[k];
+        psi[k] = (R)ph.psi[k];
+        sA[k] = (R)mx.sA[k];
+        const R Zk = -(fa2 * psi[k] + fb * Bk);
+        Lk[k] = (Zk + Bk) * izpb - Zk * iz;
+        bb[k] = Bk * ib;
+        e[k] = (a * bb[k] - R(2) * psi[k]) * ib;
+        p[k] = Zk - bb[k] * zm1 + cl * (psi[k] - a * bb[k]);
+        q[k] = -(Zk - Bk) * izb;
+        w[k] = cl * bb[k];
+        sAc[k] = cl * sA[k];
+        si[k] = bb[k] * zcm - qcr + e[k] * lc;
     }
-    const double qc = (Zc - B) * invZB;
 #pragma unroll
     for (int i = 0; i < NC; i++) {
-        const double si = bb[i] * (Zc - Zm1) - qc + e[i] * Lc;
 #pragma unroll
         for (int j = 0; j <= i; j++) {
-            const double ah = (i == j) ? sAc[i] * mx.sA[i] : cp.kk[i * NC + j] * sAc[i] * mx.sA[j];
-            J[i * (i + 1) / 2 + j] = fma(bb[i], p[j], fma(ph.psi[i], w[j], fma(e[i], Lk[j], q[j] - si - ah)));
+            R kk;
+            if constexpr (sizeof(R) == sizeof(float)) kk = cp.kkf[i * NC + j];
+            else kk = cp.kk[i * NC + j];
+            const R ah = (i == j) ? sAc[i] * sA[i] : kk * sAc[i] * sA[j];
+            J[i * (i + 1) / 2 + j] = fma(bb[i], p[j], fma(psi[i], w[j], fma(e[i], Lk[j], q[j] - si[i] - ah)));
         }
     }
+}
+
+template <int NC>
+__device__ __forceinline__ void dlnphi_dn(const Comp<NC>& cp, const Mix<NC>& mx, const double* c, const Phase<NC>& ph,
+                                          double* J) {
+    dlnphi_dn_r<NC, double>(cp, mx, ph, J);
 }
 
 // ---------------------------------------------------------------------------
@@ -625,26 +643,36 @@ __device__ __forceinline__ bool rachford_rice_f(const float* z, const float* K, 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
+// The routines below take the matrix in FP64 (H, packed lower triangle) and
+// work in R: R = float for the trust regions' model steps (factorisation,
+// triangular solves, the shift iteration), R = double where a Newton step must
+// be exact to FP64 (the split's polish once an FP32-model step fell short).
+template <class R>
+__device__ __forceinline__ R rsqrt_r(R d) {
+    if constexpr (sizeof(R) == sizeof(float)) return rsqrtf(d);
+    else return rsqrt(d);
+}
+
 // Cholesky of (H + eta diag(1)) in the scaled space; returns -1 if positive
 // definite, else the column j whose pivot d_j <= 0 (in *dfail).  Lf holds L
 // below the diagonal and 1 / L_jj on it, so that the triangular solves
 // multiply instead of divide (FP64 division costs ~7 FMA slots here).
-template <int NC>
-__device__ __forceinline__ int cholesky(const double* H, double eta, double* Lf, double* dfail) {
+template <int NC, class R>
+__device__ __forceinline__ int cholesky(const double* H, R eta, R* Lf, R* dfail) {
 #pragma unroll 1
     for (int j = 0; j < NC; j++) {
-        double d = H[tri(j, j)] + eta;
+        R d = (R)H[tri(j, j)] + eta;
 #pragma unroll 1
         for (int k = 0; k < j; k++) d = fma(-Lf[tri(j, k)], Lf[tri(j, k)], d);
-        if (!(d > 0.0)) {
+        if (!(d > R(0))) {
             *dfail = d;
             return j;
         }
-        const double inv = rsqrt(d);
+        const R inv = rsqrt_r(d);
         Lf[tri(j, j)] = inv;
 #pragma unroll 1
         for (int i = j + 1; i < NC; i++) {
-            double s = H[tri(i, j)];
+            R s = (R)H[tri(i, j)];
 #pragma unroll 1
             for (int k = 0; k < j; k++) s = fma(-Lf[tri(i, k)], Lf[tri(j, k)], s);
             Lf[tri(i, j)] = s * inv;
@@ -658,26 +686,26 @@ __device__ __forceinline__ int cholesky(const double* H, double eta, double* Lf,
 // computed part of row j, has w.(H + eta I).w = d, so the smallest eigenvalue
 // of H is at most d / ||w||^2 - eta (More and Sorensen 1983, Sec. 3).
 // Returns that bound on -lambda_min: eta - d / ||w||^2.
-template <int NC>
-__device__ __forceinline__ double shift_bound(const double* Lf, int j, double d, double eta) {
-    double w[NC], wn = 1.0;
+template <int NC, class R>
+__device__ __forceinline__ double shift_bound(const R* Lf, int j, R d, double eta) {
+    R w[NC], wn = R(1);
 #pragma unroll 1
     for (int i = j - 1; i >= 0; i--) {
-        double s = -Lf[tri(j, i)];
+        R s = -Lf[tri(j, i)];
 #pragma unroll 1
         for (int k = i + 1; k < j; k++) s = fma(-Lf[tri(k, i)], w[k], s);
         w[i] = s * Lf[tri(i, i)];
         wn = fma(w[i], w[i], wn);
     }
-    return eta - d / wn;
+    return eta - (double)d / (double)wn;
 }
 
 // Solve L y = b (forward) in place
-template <int NC>
-__device__ __forceinline__ void fwd(const double* Lf, double* b) {
+template <int NC, class R>
+__device__ __forceinline__ void fwd(const R* Lf, R* b) {
 #pragma unroll 1
     for (int i = 0; i < NC; i++) {
-        double s = b[i];
+        R s = b[i];
 #pragma unroll 1
         for (int k = 0; k < i; k++) s = fma(-Lf[tri(i, k)], b[k], s);
         b[i] = s * Lf[tri(i, i)];
@@ -685,11 +713,11 @@ __device__ __forceinline__ void fwd(const double* Lf, double* b) {
 }
 
 // Solve L^T x = b (backward) in place
-template <int NC>
-__device__ __forceinline__ void bwd(const double* Lf, double* b) {
+template <int NC, class R>
+__device__ __forceinline__ void bwd(const R* Lf, R* b) {
 #pragma unroll 1
     for (int i = NC - 1; i >= 0; i--) {
-        double s = b[i];
+        R s = b[i];
 #pragma unroll 1
         for (int k = i + 1; k < NC; k++) s = fma(-Lf[tri(k, i)], b[k], s);
         b[i] = s * Lf[tri(i, i)];
@@ -699,7 +727,8 @@ __device__ __forceinline__ void bwd(const double* Lf, double* b) {
 // Trust-region subproblem (Appendix B): minimise gs.u + u.Hs.u/2 subject to
 // ||u|| <= radius in the scaled space, by Hebden's iteration on the shift eta
 // of (Hs + eta I) u = -gs (Hebden 1973; More and Sorensen 1983), solved to
-// 1e-10 relative on ||u||.
+// kShiftTol relative on ||u|| (1e-10 in FP64, 1e-4 in FP32: the radius is a
+// safeguard, so a step within 1e-4 of it serves as well).
 //
 // One call does one factorisation, so a persistent kernel spends one
 // factorisation per lane per trip and a lane that needs many shifts does not
@@ -718,14 +747,16 @@ __device__ __forceinline__ void bwd(const double* Lf, double* b) {
 //    is concave), so the first starts from the eta = 0 factorisation, and a
 //    caller that shrank the radius around the same H passes the previous shift
 //    as a further lower bound.
-//  - the iteration also stops once the bracket has closed to 1e-12 relative:
-//    with the shift at the pole -lambda_min (the nearly hard case) ||u|| can
-//    change by 1e-8 relative for the smallest change of eta.
+//  - the iteration also stops once the bracket has closed to 1e-12 relative
+//    (1e-6 in FP32): with the shift at the pole -lambda_min (the nearly hard
+//    case) ||u|| can change by 1e-8 relative for the smallest change of eta.
 // A radius <= 0 is not yet set: it becomes ||Newton step|| when H is positive
 // definite, else 1.  Returns 1 with the step in u (the shift used in sh.eta),
 // 0 if the iteration continues on the next call, and -1 with newton_only when
-// H is not positive definite.
-constexpr double kTRShiftTol = 1e-10;
+// H is not positive definite, or when the solve failed: a factorisation that
+// fails even at the upper end of the bracket (a matrix that is not finite in
+// R) would otherwise repeat forever, so past kTRShiftCap + 2 calls the solve
+// gives up (the solve is then over: sh.active = 0).
 constexpr int kTRShiftCap = 40;
 
 struct TRShift {
@@ -733,19 +764,28 @@ struct TRShift {
     int active, it;
 };
 
-template <int NC>
+template <int NC, class R>
 __device__ __forceinline__ int tr_shift_step(const double* Hs, const double* gs, double& radius, double eta_lo,
-                                             bool newton_only, TRShift& sh, double* Lf, double* u) {
+                                             bool newton_only, TRShift& sh, R* Lf, double* u) {
+    constexpr double kShiftTol = sizeof(R) == sizeof(float) ? 1e-4 : 1e-10;
+    constexpr double kPoleTol = sizeof(R) == sizeof(float) ? 1e-6 : 1e-12;
+    if (sh.active && sh.it > kTRShiftCap + 2) {
+        sh.active = 0;
+        return -1;
+    }
     const double eta = sh.active ? sh.eta : 0.0;
-    double dfail = 0.0;
-    const int jf = cholesky<NC>(Hs, eta, Lf, &dfail);
+    R dfail = R(0);
+    const int jf = cholesky<NC, R>(Hs, (R)eta, Lf, &dfail);
     const bool pd = jf < 0;
     double un = 0.0;
+    R ur[NC];
     if (pd) {
 #pragma unroll
-        for (int i = 0; i < NC; i++) u[i] = -gs[i];
-        fwd<NC>(Lf, u);
-        bwd<NC>(Lf, u);
+        for (int i = 0; i < NC; i++) ur[i] = (R)(-gs[i]);
+        fwd<NC, R>(Lf, ur);
+        bwd<NC, R>(Lf, ur);
+#pragma unroll
+        for (int i = 0; i < NC; i++) u[i] = (double)ur[i];
         if (newton_only) return 1;
 #pragma unroll
         for (int i = 0; i < NC; i++) un = fma(u[i], u[i], un);
@@ -756,7 +796,7 @@ __device__ __forceinline__ int tr_shift_step(const double* Hs, const double* gs,
                 sh.eta = 0.0;
                 return 1;
             }
-        } else if (fabs(un - radius) <= kTRShiftTol * radius || sh.it >= kTRShiftCap) {
+        } else if (fabs(un - radius) <= kShiftTol * radius || sh.it >= kTRShiftCap) {
             sh.active = 0;
             return 1;
         }
@@ -786,7 +826,7 @@ __device__ __forceinline__ int tr_shift_step(const double* Hs, const double* gs,
         // eigenvalue bound from the failed pivot, then the safeguarded
         // midpoint of the bracket; past the cap the upper end, where H + eta I
         // is positive definite, so that the next call ends the solve
-        sh.elo = fmax(sh.elo, shift_bound<NC>(Lf, jf, dfail, eta));
+        sh.elo = fmax(sh.elo, shift_bound<NC, R>(Lf, jf, dfail, eta));
         if (!(sh.ehi > sh.elo)) sh.ehi = 2.0 * sh.elo + 1e-300;
         sh.eta = sh.it >= kTRShiftCap ? sh.ehi
                                       : fmax(sqrt(fmax(sh.elo, 1e-300) * sh.ehi), sh.elo + 1e-3 * (sh.ehi - sh.elo));
@@ -796,17 +836,18 @@ __device__ __forceinline__ int tr_shift_step(const double* Hs, const double* gs,
     // positive definite, ||u|| off the radius: Newton step on the secular equation
     if (un < radius) sh.ehi = eta;
     else sh.elo = fmax(sh.elo, eta);
-    if (sh.ehi - sh.elo <= 1e-12 * sh.ehi) {  // shift pinned at the pole: ||u|| is as close as it gets
+    if (sh.ehi - sh.elo <= kPoleTol * sh.ehi) {  // shift pinned at the pole: ||u|| is as close as it gets
         sh.active = 0;
         sh.eta = eta;
         return 1;
     }
-    double q[NC], qn = 0.0;
+    R q[NC];
+    double qn = 0.0;
 #pragma unroll
-    for (int i = 0; i < NC; i++) q[i] = u[i];
-    fwd<NC>(Lf, q);
+    for (int i = 0; i < NC; i++) q[i] = ur[i];
+    fwd<NC, R>(Lf, q);
 #pragma unroll
-    for (int i = 0; i < NC; i++) qn = fma(q[i], q[i], qn);
+    for (int i = 0; i < NC; i++) qn = fma((double)q[i], (double)q[i], qn);
     double en = eta + (un * un / qn) * (un - radius) / radius;
     if (un > radius) en = fmax(en, sh.elo);
     if (!(en >= sh.elo && en < sh.ehi)) {  // out of the bracket: geometric midpoint

@@ -861,8 +861,9 @@ __device__ __forceinline__ bool stab_point(const Comp<NC>& cp, const Mix<NC>& mx
     }
     p.tm = t;
     if (!isfinite(t)) return false;
+    // H_ij = sqrt(W_i W_j) J_ij / sum W + delta_ij (1 + gt_i / 2)
     double J[NC * (NC + 1) / 2];
-    dlnphi_dn<NC>(cp, mx, c, ph, J);
+    dlnphi_dn_r<NC, double>(cp, mx, ph, J);
 #pragma unroll
     for (int i = 0; i < NC; i++) p.g[i] = sW[i] * p.gt[i];
 #pragma unroll
@@ -882,7 +883,7 @@ __device__ __forceinline__ bool stab_point(const Comp<NC>& cp, const Mix<NC>& mx
 template <int NC>
 struct StabTR {
     int64_t m, item;
-    int t, it, iters, phase;  // phase 0: evaluate the start point; 1: iterate
+    int t, it, iters, phase, idle;  // phase 0: evaluate the start point; 1: iterate; idle: trips without evaluation
     int32_t fl;
     Mix<NC> mx;
     double d[NC], beta[NC], radius, eta_lo;
@@ -903,7 +904,7 @@ struct StabTR {
             cur.lnW[i] = ws.lnW[(t * NC + i) * n + m];
         }
         fl = ws.tflag[t * n + m];
-        it = iters = phase = 0;
+        it = iters = phase = idle = 0;
         radius = -1.0;
         eta_lo = 0.0;
         sh.active = 0;
@@ -936,8 +937,19 @@ struct StabTR {
             int r = 0;
 #pragma unroll 1
             for (int k = 0; k < (tail ? kTRShiftCap + 2 : 1) && r == 0; k++)
-                r = tr_shift_step<NC>(cur.H, cur.g, radius, eta_lo, false, sh, Lf, u);
-            if (r == 0) return 0;
+                r = tr_shift_step<NC, double>(cur.H, cur.g, radius, eta_lo, false, sh, Lf, u);
+            if (r == 0) {
+                // a solve takes at most kTRShiftCap + 3 calls; the budget bounds a run whatever happens
+                if (++idle > (ws.ctl.tr_stab + 2) * (kTRShiftCap + 3)) {
+                    store(ws, 1, 0);
+                    return 1;
+                }
+                return 0;
+            }
+            if (r < 0) {  // the solve failed (a model that is not finite): stop at the current point
+                store(ws, 1, 0);
+                return 1;
+            }
             for (int i = 0; i < NC; i++) {
                 double hd = 0.0;
                 for (int j = 0; j < NC; j++) hd = fma(cur.H[i >= j ? tri(i, j) : tri(j, i)], u[j], hd);
@@ -1412,54 +1424,62 @@ struct SplitPt {
     double Hs[NC * (NC + 1) / 2];  // S H S
 };
 
+// Evaluation of a split point in FP64 (every decision rests on it): the
+// phases, their EOS, the gradient gt = mu^V - mu^L (Eq. split_grad), G
+// (Eq. gibbs) and the scaling S_i = (z_i / (x_i y_i))^(-1/2) of
+// u = D^(1/2) dn^V.  w = 1 / (theta (1 - theta)), pl and pv feed split_model.
 template <int NC>
-__device__ __forceinline__ bool split_point(const Comp<NC>& cp, const Mix<NC>& mx, const double* z, const double* iz,
-                                            const double* nV, SplitPt<NC>& p) {
+__device__ __forceinline__ bool split_eval(const Comp<NC>& cp, const Mix<NC>& mx, const double* z, const double* iz,
+                                           const double* nV, SplitPt<NC>& p, Phase<NC>& pl, Phase<NC>& pv,
+                                           double& w) {
     double th = 0.0;
 #pragma unroll
     for (int i = 0; i < NC; i++) th += nV[i];
     p.th = th;
-    // one division: w = 1 / (theta (1 - theta)), 1 / theta = w (1 - theta), 1 / (1 - theta) = w theta
-    const double w = 1.0 / (th * (1.0 - th));
+    // one division: w, then 1 / theta = w (1 - theta), 1 / (1 - theta) = w theta
+    w = 1.0 / (th * (1.0 - th));
     const double iv = w * (1.0 - th), il = w * th;
 #pragma unroll
     for (int i = 0; i < NC; i++) {
         p.y[i] = nV[i] * iv;
         p.x[i] = (z[i] - nV[i]) * il;
     }
-    Phase<NC> pl, pv;
     eos<NC>(cp, mx, p.x, pl);
     eos<NC>(cp, mx, p.y, pv);
     p.ZL = pl.Z;
     p.ZV = pv.Z;
-    double JL[NC * (NC + 1) / 2], JV[NC * (NC + 1) / 2];
-    dlnphi_dn<NC>(cp, mx, p.x, pl, JL);
-    dlnphi_dn<NC>(cp, mx, p.y, pv, JV);
     double G = 0.0;
 #pragma unroll
     for (int i = 0; i < NC; i++) {
         double mul = log_fast(p.x[i]) + pl.lnphi[i], muv = log_fast(p.y[i]) + pv.lnphi[i];
         p.gt[i] = muv - mul;
         G = fma(z[i] - nV[i], mul, fma(nV[i], muv, G));
-    }
-    p.G = G;
-    // scaling S_i = (z_i / (x_i y_i))^(-1/2) of u = D^(1/2) dn^V; the diagonal
-    // term z_i / (x_i y_i) of the Hessian then scales to exactly 1
-#pragma unroll
-    for (int i = 0; i < NC; i++) {
         p.S[i] = sqrt(p.x[i] * p.y[i] * iz[i]);
         p.gs[i] = p.S[i] * p.gt[i];
     }
+    p.G = G;
+    return isfinite(G);
+}
+
+// The trust region's model at an evaluated point: the scaled Hessian
+// S H S (Eq. split_hess, reading R5) from both phases' n_T d ln phi / dn,
+// formed in R.  The diagonal term z_i / (x_i y_i) of H scales to exactly 1.
+template <int NC, class R>
+__device__ __forceinline__ void split_model(const Comp<NC>& cp, const Mix<NC>& mx, const Phase<NC>& pl,
+                                            const Phase<NC>& pv, double w, SplitPt<NC>& p) {
+    R JL[NC * (NC + 1) / 2], JV[NC * (NC + 1) / 2];
+    dlnphi_dn_r<NC, R>(cp, mx, pl, JL);
+    dlnphi_dn_r<NC, R>(cp, mx, pv, JV);
+    const R th = (R)p.th, th1 = (R)(1.0 - p.th);
 #pragma unroll
     for (int i = 0; i < NC; i++) {
-        const double wSi = w * p.S[i];
+        const R wSi = (R)(w * p.S[i]);
 #pragma unroll
         for (int j = 0; j <= i; j++) {
-            const double h = th * JL[tri(i, j)] + (1.0 - th) * JV[tri(i, j)] - 1.0;
-            p.Hs[tri(i, j)] = (i == j) ? fma(wSi * p.S[i], h, w) : wSi * p.S[j] * h;
+            const R h = th * JL[tri(i, j)] + th1 * JV[tri(i, j)] - R(1);
+            p.Hs[tri(i, j)] = (i == j) ? fma((double)(wSi * (R)p.S[i]), (double)h, w) : (double)(wSi * (R)p.S[j] * h);
         }
     }
-    return isfinite(G);
 }
 
 // 0.99 fraction-to-boundary cut keeping 0 < n^V_i + d_i < z_i: the smallest
@@ -1487,7 +1507,7 @@ __device__ __forceinline__ double boundary_cut(const double* z, const double* nV
 template <int NC>
 struct SplitTR {
     int64_t m;
-    int it, iters, newton_steps, phase;  // phase 0: start point; 1: trust region; 2: Newton polish
+    int it, iters, newton_steps, phase, trips;  // phase 0: start point; 1: trust region; 2: Newton polish
     int32_t st;
     Mix<NC> mx;
     double z[NC], iz[NC], nV[NC], radius, eta_lo;  // iz = 1 / z
@@ -1507,7 +1527,7 @@ struct SplitTR {
             nV[i] = ws.nV[i * n + m];
         }
         st = io.status[m];
-        it = iters = newton_steps = phase = 0;
+        it = iters = newton_steps = phase = trips = 0;
         radius = -1.0;
         eta_lo = 0.0;
         sh.active = 0;
@@ -1528,10 +1548,19 @@ struct SplitTR {
         return 1;
     }
 
-    // 0 continue, 1 done
+    // 0 continue, 1 done.  The model stays FP64 here: the Newton polish must
+    // land well inside the 1e-10 residual for the outputs to agree with
+    // another FP64 implementation to 1e-8 (an FP32 model's polish step stops
+    // at ~1e-11, which ill-conditioned splits turn into 1e-7 in beta).  Every
+    // trip evaluates a point or ends the run but for a solve that needs more
+    // than a trip; a budget of trips bounds the run whatever happens.
     template <class CS>
     __device__ __forceinline__ int step(const CS& cs, const WS& ws, const IO& io) {
         const Comp<NC>& cp = cs.of(m);
+        if (++trips > ws.ctl.tr_split + ws.ctl.polish + 8) {
+            st |= ST_MAXITER;
+            return finish(io, 0);
+        }
         double u[NC], dstep[NC], trial[NC], pred = 0.0;
         if (phase == 0) {
 #pragma unroll
@@ -1543,10 +1572,10 @@ struct SplitTR {
             int r = 0;
 #pragma unroll 1
             for (int k = 0; k < kTRShiftCap + 2 && r == 0; k++)
-                r = tr_shift_step<NC>(cur.Hs, cur.gs, radius, eta_lo, phase == 2, sh, Lf, u);
+                r = tr_shift_step<NC, double>(cur.Hs, cur.gs, radius, eta_lo, phase == 2, sh, Lf, u);
             if (r == 0) return 0;
-            if (r < 0) {  // Newton polish on an indefinite Hessian: stop here
-                if (maxabs<NC>(cur.gt) > ws.ctl.tol_fug) st |= ST_MAXITER;
+            if (r < 0) {  // Newton polish on an indefinite Hessian, or a failed solve: stop here
+                if (phase == 1 || maxabs<NC>(cur.gt) > ws.ctl.tol_fug) st |= ST_MAXITER;
                 return finish(io, 0);
             }
 #pragma unroll
@@ -1570,7 +1599,13 @@ struct SplitTR {
             for (int i = 0; i < NC; i++) trial[i] = nV[i] + dstep[i];
         }
         SplitPt<NC> nxt;
-        const bool ok = split_point<NC>(cp, mx, z, iz, trial, nxt);
+        bool ok;
+        {
+            Phase<NC> pl, pv;
+            double w;
+            ok = split_eval<NC>(cp, mx, z, iz, trial, nxt, pl, pv, w);
+            if (ok) split_model<NC, double>(cp, mx, pl, pv, w, nxt);
+        }
         if (phase == 0) {
             if (!ok) return finish(io, 1);
             cur = nxt;
