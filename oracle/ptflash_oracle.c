@@ -61,7 +61,10 @@
  *       single-phase with the COLLAPSE status bit.  An SS run that reaches
  *       its cap with theta outside (0,1) starts the trust region from the
  *       feasible material-balance point n^V_i = t K_i z_i / (1 + t (K_i - 1))
- *       at t = 1/2.
+ *       at t = 1/2.  A trust-region iterate whose theta comes within 1e-10
+ *       of 0 or 1 has collapsed onto one phase without converging (each
+ *       fraction-to-boundary step then moves theta six decades further): the
+ *       run stops there, single-phase with the COLLAPSE and MAXITER bits.
  *   R14 Canonical phase labels: after a two-phase result, if Z(y) < Z(x)
  *       the phases are swapped (y is always the lower-density phase).
  *   R15 Single phase output: beta = 0, x = y = z, K = 1.
@@ -104,6 +107,7 @@
 #define NPRECHECK 3           /* Sec. 2.2.3 */
 #define EPS_NEG 1e-10         /* R8 */
 #define TRIVIAL_LNK 1e-6      /* R13 */
+#define COLLAPSE_TH 1e-10     /* R13: trust-region iterate collapsed onto one phase */
 #define PRED_TRUST 1e-12      /* R9: ratio test trusted above this relative size */
 
 /* ------------------------------------------------------------------------ */
@@ -847,6 +851,11 @@ static void or_split(const or_mix* m, const double* z, double* lnK, or_result* r
     int it = 0, phase_newton = 0, newton_steps = 0;
     for (;;) {
         double res = maxabs(nc, cur.gt);
+        if (!(cur.th > COLLAPSE_TH && cur.th < 1.0 - COLLAPSE_TH)) {  /* R13 */
+            r->status |= ST_MAXITER | ST_COLLAPSE;
+            set_single(nc, z, r);
+            return;
+        }
         if (phase_newton) {
             if (res <= TOL_FUG && newton_steps >= 1) break;
             if (newton_steps == KNEWTON_POLISH) { r->status |= ST_MAXITER; break; }
