@@ -42,6 +42,11 @@ constexpr int kNewtonPolish = 10;     // Newton steps after a split TR run
 constexpr int kPrecheck = 3;          // Sec. 2.2.3
 constexpr double kEpsNeg = 1e-10;     // "negative" tm / tpd / Delta G
 constexpr double kTrivialLnK = 1e-6;  // split collapsed to K = 1
+// A split trust-region iterate with theta this close to 0 or 1 has collapsed
+// onto one phase without converging (each fraction-to-boundary step then moves
+// theta some six decades further): the run stops there, single phase, not
+// converged.
+constexpr double kCollapseTheta = 1e-10;
 constexpr double kPredTrust = 1e-12;  // ratio test trusted above this
 // Learned form: a split started from the initializer's K keeps its result only
 // if its converged ln K lie within this distance of the network's prediction

@@ -1533,9 +1533,13 @@ struct SplitTR {
         sh.active = 0;
     }
 
-    __device__ __forceinline__ int finish(const IO& io, int kind) {  // kind 0 result, 1 non-finite
+    // kind 0 result, 1 non-finite, 2 collapsed onto one phase without converging
+    __device__ __forceinline__ int finish(const IO& io, int kind) {
         if (kind == 1) {
             st |= ST_NONFINITE;
+            write_single<NC>(io, m, z);
+        } else if (kind == 2) {
+            st |= ST_COLLAPSE | ST_MAXITER;
             write_single<NC>(io, m, z);
         } else if (!(cur.th > 0.0 && cur.th < 1.0)) {
             st |= ST_COLLAPSE;
@@ -1632,6 +1636,7 @@ struct SplitTR {
             else if (rho >= 0.75) radius *= 2.0;
             iters = ++it;
         }
+        if (!(cur.th > kCollapseTheta && cur.th < 1.0 - kCollapseTheta)) return finish(io, 2);
         const double res = maxabs<NC>(cur.gt);
         if (phase == 1 && res < ws.ctl.tol_split_tr) phase = 2;
         if (phase == 2) {
