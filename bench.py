@@ -53,7 +53,7 @@ LEARNED_DESC = ("10 SRK pseudo-components drawn as above, 1e7 mixtures, T~U(250,
 # k_split_tr on 3e5 mixtures, 70,791 split trust-region mixtures, 859.1 MB);
 # the bench scales it by this run's units.  Only valid for the kernel as
 # captured: set to {} when the kernel changes until it is captured again.
-TRAFFIC_PER_UNIT = {"split_tr": (859.092e6 / 70791, "split trust-region mixtures", lambda q: q["split_tr"])}
+TRAFFIC_PER_UNIT = {}
 
 
 def measured_hbm_gbs():

@@ -93,7 +93,13 @@ typedef struct {
     double nn_lnk_dev;    /* learned form: a split started from the initializer's K is kept only if every
                              converged ln K_i lies within this distance of the network's (default 0.3);
                              otherwise the plain method redoes the mixture */
-    int32_t reserved[2];
+    int32_t tr_lanes;     /* lanes per trust-region run: 0 (default) one lane per run while a trust-region
+                             queue lasts, then, once a warp's queue has drained, several lanes per run
+                             (one per component) for the runs it has left; 1 one lane throughout; 2 several
+                             lanes throughout.  The results are the same bit for bit in every mode (an
+                             implementation choice, no counterpart in the paper); other values are
+                             PTF_ERR_INVALID_ARG */
+    int32_t reserved;
 } ptflash_options;
 
 /* Fill *opt with the defaults (plain method).  PTF_ERR_INVALID_ARG if NULL. */

@@ -285,8 +285,9 @@ static int parse_options(const ptflash_ctx* c, const ptflash_options* opt, CallO
         !cap(opt->max_ss_split, o.ctl.ss_split) || !cap(opt->max_tr_split, o.ctl.tr_split) ||
         !cap(opt->max_polish, o.ctl.polish) || !tol(opt->tol_stab, o.ctl.tol_stab) ||
         !tol(opt->tol_split_tr, o.ctl.tol_split_tr) || !tol(opt->tol_fug, o.ctl.tol_fug) ||
-        !tol(opt->nn_lnk_dev, o.ctl.nn_lnk_dev))
+        !tol(opt->nn_lnk_dev, o.ctl.nn_lnk_dev) || opt->tr_lanes < 0 || opt->tr_lanes > 2)
         return PTF_ERR_INVALID_ARG;
+    o.ctl.tr_coop = opt->tr_lanes;
     if (opt->use_nn) {
         if (!(opt->p_l >= 0.0 && opt->p_l <= opt->p_r && opt->p_r <= 1.0)) return PTF_ERR_INVALID_ARG;
         if (!c->nn[0].ready || !c->nn[1].ready) return PTF_ERR_NOT_READY;

@@ -61,6 +61,10 @@ struct Ctl {
     int ss_stab = kSSStab, tr_stab = kTRStab, ss_split = kSSSplit, tr_split = kTRSplit, polish = kNewtonPolish;
     double tol_stab = kTolStab, tol_split_tr = kTolSplitTR, tol_fug = kTolFug;
     double nn_lnk_dev = kNNLnKDev;  // learned form: accepted max |ln K - ln K_net| of a network-started split
+    // trust-region lanes per run: 0 one lane per run until the queue drains,
+    // then several lanes per run; 1 one lane throughout; 2 several lanes
+    // throughout (the results are the same bit for bit in every mode)
+    int tr_coop = 0;
 };
 
 // status bits (same values as documented in include/ptflash.h)
@@ -338,6 +342,18 @@ __device__ __forceinline__ Root cubic_select(double A, double B) {
 // ln phi_i = B_i [(Z - 1)/B + A L / B^2] - ln(Z - B) - psi_i (2 L / B),
 // psi_i = sqrt(A_i) sum_j (1 - k_ij) sqrt(A_j) c_j.
 // ---------------------------------------------------------------------------
+// ln phi_i = B_i u - ln(Z - B) - psi_i v with u = [(Z - 1) + A L / B] / B and
+// v = 2 L / B: the scalar coefficients, then one row (shared by the one-lane
+// and the several-lanes-per-run evaluations, so both round alike)
+__device__ __forceinline__ void lnphi_coef(double A, double B, const Root& r, double& u, double& v) {
+    const double invB = 1.0 / B;
+    u = ((r.Z - 1.0) + A * r.L * invB) * invB;
+    v = 2.0 * r.L * invB;
+}
+__device__ __forceinline__ double lnphi_row(double Bi, double psi, double u, double v, double lzb) {
+    return fma(Bi, u, -lzb) - psi * v;
+}
+
 template <int NC>
 struct Phase {
     double A, B, Z, L;
@@ -362,11 +378,10 @@ __device__ __forceinline__ void eos(const Comp<NC>& cp, const Mix<NC>& mx, const
         B = fma(c[i], mx.B[i], B);
     }
     Root r = cubic_select(A, B);
-    double invB = 1.0 / B;
-    double u = ((r.Z - 1.0) + A * r.L * invB) * invB;
-    double v = 2.0 * r.L * invB;
+    double u, v;
+    lnphi_coef(A, B, r, u, v);
 #pragma unroll
-    for (int i = 0; i < NC; i++) ph.lnphi[i] = fma(mx.B[i], u, -r.lzb) - ph.psi[i] * v;
+    for (int i = 0; i < NC; i++) ph.lnphi[i] = lnphi_row(mx.B[i], ph.psi[i], u, v, r.lzb);
     ph.A = A;
     ph.B = B;
     ph.Z = r.Z;
@@ -385,45 +400,110 @@ __device__ __forceinline__ void eos(const Comp<NC>& cp, const Mix<NC>& mx, const
 // trust regions' model (the Hessians only shape the steps; every point the
 // steps reach is evaluated, and every decision taken, in FP64): the scalar
 // prelude, where Z - B and the derivative of the cubic can cancel, stays FP64.
-template <int NC, class R>
-__device__ __forceinline__ void dlnphi_dn_r(const Comp<NC>& cp, const Mix<NC>& mx, const Phase<NC>& ph, R* J) {
-    const double A = ph.A, B = ph.B, Z = ph.Z, L = ph.L;
-    const double FZ = fma(fma(3.0, Z, -2.0), Z, A - B - B * B);
-    const double FA = Z - B, FB = -Z - 2.0 * B * Z - A;
+// The scalar prelude, the per-component vectors and one entry, shared by the
+// one-lane and the several-lanes-per-run evaluations.  Every product and sum
+// is explicit (round-to-nearest intrinsics, which are never fused, or fma),
+// so the compiler cannot contract them differently in the two contexts and
+// both give the same bits.
+template <class R>
+__device__ __forceinline__ R mul_rn(R a, R b) {
+    if constexpr (sizeof(R) == sizeof(float)) return __fmul_rn(a, b);
+    else return __dmul_rn(a, b);
+}
+template <class R>
+__device__ __forceinline__ R add_rn(R a, R b) {
+    if constexpr (sizeof(R) == sizeof(float)) return __fadd_rn(a, b);
+    else return __dadd_rn(a, b);
+}
+template <class R>
+__device__ __forceinline__ R sub_rn(R a, R b) {
+    if constexpr (sizeof(R) == sizeof(float)) return __fsub_rn(a, b);
+    else return __dsub_rn(a, b);
+}
+
+template <class R>
+struct DlnPre {
+    R fa2, fb, izpb, iz, ib, izb, a, zm1, cl, zcm, lc, qcr;
+};
+
+template <class R>
+__device__ __forceinline__ DlnPre<R> dln_prelude(double A, double B, double Z, double L) {
+    const double FZ = fma(fma(3.0, Z, -2.0), Z, fma(-B, B, sub_rn(A, B)));  // f'(Z)
+    const double FA = sub_rn(Z, B), FB = sub_rn(fma(-2.0 * B, Z, -Z), A);
     // the five reciprocals 1/B, 1/(Z-B), 1/(Z+B), 1/Z, 1/FZ from one division
     // (each product of the others and the reciprocal of the whole product)
-    const double p1 = B * FA, p2 = p1 * (Z + B), p3 = p2 * Z;
-    const double r4 = 1.0 / (p3 * FZ);
-    const double invFZ = r4 * p3, r3 = r4 * FZ;
-    const double invZ = r3 * p2, r2 = r3 * Z;
-    const double invZpB = r2 * p1, r1 = r2 * (Z + B);
-    const double invZB = r1 * B, invB = r1 * FA;
-    const double cL = 2.0 * L * invB;  // 2 L / B
-    const double Zm1 = Z - 1.0;
+    const double ZpB = add_rn(Z, B);
+    const double p1 = mul_rn(B, FA), p2 = mul_rn(p1, ZpB), p3 = mul_rn(p2, Z);
+    const double r4 = 1.0 / mul_rn(p3, FZ);
+    const double invFZ = mul_rn(r4, p3), r3 = mul_rn(r4, FZ);
+    const double invZ = mul_rn(r3, p2), r2 = mul_rn(r3, Z);
+    const double invZpB = mul_rn(r2, p1), r1 = mul_rn(r2, ZpB);
+    const double invZB = mul_rn(r1, B), invB = mul_rn(r1, FA);
+    const double cL = mul_rn(2.0 * L, invB);  // 2 L / B
+    const double Zm1 = sub_rn(Z, 1.0);
     // Zc = sum c_k Z_k, Lc = sum c_k L_k
-    const double Zc = -(FA * 2.0 * A + FB * B) * invFZ;
-    const double Lc = (Zc + B) * invZpB - Zc * invZ;
-    const double qc = (Zc - B) * invZB;
-    // f_ij = bb_i p_j + q_j + psi_i w_j + e_i L_j - cL Ahat_ij with
-    //   p_j = Z_j - bb_j (Z - 1) + cL (psi_j - A bb_j), q_j = -(Z_j - B_j)/(Z - B),
-    //   w_j = cL bb_j; the row sum of c_k f_ik is s_i (closed form).
-    const R fa2 = (R)(2.0 * FA * invFZ), fb = (R)(FB * invFZ), izpb = (R)invZpB, iz = (R)invZ, ib = (R)invB,
-            izb = (R)invZB, a = (R)A, zm1 = (R)Zm1, cl = (R)cL, zcm = (R)(Zc - Zm1), lc = (R)Lc, qcr = (R)qc;
-    R bb[NC], p[NC], q[NC], w[NC], e[NC], Lk[NC], sAc[NC], sA[NC], psi[NC], si[NC];
+    const double Zc = mul_rn(-fma(FA, 2.0 * A, mul_rn(FB, B)), invFZ);
+    const double Lc = fma(add_rn(Zc, B), invZpB, -mul_rn(Zc, invZ));
+    const double qc = mul_rn(sub_rn(Zc, B), invZB);
+    DlnPre<R> c;
+    c.fa2 = (R)mul_rn(2.0 * FA, invFZ);
+    c.fb = (R)mul_rn(FB, invFZ);
+    c.izpb = (R)invZpB;
+    c.iz = (R)invZ;
+    c.ib = (R)invB;
+    c.izb = (R)invZB;
+    c.a = (R)A;
+    c.zm1 = (R)Zm1;
+    c.cl = (R)cL;
+    c.zcm = (R)sub_rn(Zc, Zm1);
+    c.lc = (R)Lc;
+    c.qcr = (R)qc;
+    return c;
+}
+
+// f_ij = bb_i p_j + q_j + psi_i w_j + e_i L_j - cL Ahat_ij with
+//   p_j = Z_j - bb_j (Z - 1) + cL (psi_j - A bb_j), q_j = -(Z_j - B_j)/(Z - B),
+//   w_j = cL bb_j; the row sum of c_k f_ik is s_i (closed form).
+template <class R>
+struct DlnVec {
+    R bb, p, q, w, e, Lk, sAc, si;
+};
+
+template <class R>
+__device__ __forceinline__ DlnVec<R> dln_vec(const DlnPre<R>& c, R Bk, R psik, R sAk) {
+    DlnVec<R> v;
+    const R Zk = -fma(c.fa2, psik, mul_rn<R>(c.fb, Bk));
+    v.Lk = fma(add_rn<R>(Zk, Bk), c.izpb, -mul_rn<R>(Zk, c.iz));
+    v.bb = mul_rn<R>(Bk, c.ib);
+    const R abb = mul_rn<R>(c.a, v.bb);
+    v.e = mul_rn<R>(sub_rn<R>(abb, R(2) * psik), c.ib);
+    v.p = fma(c.cl, sub_rn<R>(psik, abb), fma(-v.bb, c.zm1, Zk));
+    v.q = mul_rn<R>(sub_rn<R>(Bk, Zk), c.izb);
+    v.w = mul_rn<R>(c.cl, v.bb);
+    v.sAc = mul_rn<R>(c.cl, sAk);
+    v.si = fma(v.e, c.lc, fma(v.bb, c.zcm, -c.qcr));
+    return v;
+}
+
+// entry (i, j), j <= i: row quantities of i, column quantities of j, and
+// cL Ahat_ij = ah1 ah2.  Every operation is explicit (fma, or a subtraction
+// of two values that are no products), so the compiler cannot contract it
+// differently where i == j is known at compile time and where it is not.
+template <class R>
+__device__ __forceinline__ R dln_entry(R bbi, R psii, R ei, R sii, R pj, R wj, R Lj, R qj, R ah1, R ah2) {
+    return fma(bbi, pj, fma(psii, wj, fma(ei, Lj, fma(-ah1, ah2, qj - sii))));
+}
+
+template <int NC, class R>
+__device__ __forceinline__ void dlnphi_dn_r(const Comp<NC>& cp, const Mix<NC>& mx, const Phase<NC>& ph, R* J) {
+    const DlnPre<R> c = dln_prelude<R>(ph.A, ph.B, ph.Z, ph.L);
+    DlnVec<R> v[NC];
+    R sA[NC], psi[NC];
 #pragma unroll
     for (int k = 0; k < NC; k++) {
-        const R Bk = (R)mx.B[k];
         psi[k] = (R)ph.psi[k];
         sA[k] = (R)mx.sA[k];
-        const R Zk = -(fa2 * psi[k] + fb * Bk);
-        Lk[k] = (Zk + Bk) * izpb - Zk * iz;
-        bb[k] = Bk * ib;
-        e[k] = (a * bb[k] - R(2) * psi[k]) * ib;
-        p[k] = Zk - bb[k] * zm1 + cl * (psi[k] - a * bb[k]);
-        q[k] = -(Zk - Bk) * izb;
-        w[k] = cl * bb[k];
-        sAc[k] = cl * sA[k];
-        si[k] = bb[k] * zcm - qcr + e[k] * lc;
+        v[k] = dln_vec<R>(c, (R)mx.B[k], psi[k], sA[k]);
     }
 #pragma unroll
     for (int i = 0; i < NC; i++) {
@@ -432,8 +512,9 @@ __device__ __forceinline__ void dlnphi_dn_r(const Comp<NC>& cp, const Mix<NC>& m
             R kk;
             if constexpr (sizeof(R) == sizeof(float)) kk = cp.kkf[i * NC + j];
             else kk = cp.kk[i * NC + j];
-            const R ah = (i == j) ? sAc[i] * sA[i] : kk * sAc[i] * sA[j];
-            J[i * (i + 1) / 2 + j] = fma(bb[i], p[j], fma(psi[i], w[j], fma(e[i], Lk[j], q[j] - si[i] - ah)));
+            const R ah1 = (i == j) ? v[i].sAc : mul_rn<R>(kk, v[i].sAc);  // cL Ahat_ij = ah1 sA_j
+            J[i * (i + 1) / 2 + j] =
+                dln_entry<R>(v[i].bb, psi[i], v[i].e, v[i].si, v[j].p, v[j].w, v[j].Lk, v[j].q, ah1, sA[j]);
         }
     }
 }

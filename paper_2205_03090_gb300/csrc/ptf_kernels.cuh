@@ -24,6 +24,7 @@
 // of consecutive mixtures reads and writes coalesced 256-byte rows.
 #pragma once
 #include "ptf_device.cuh"
+#include "ptf_group.cuh"
 
 namespace ptf {
 
@@ -835,6 +836,14 @@ struct StabPt {
     double H[NC * (NC + 1) / 2];
 };
 
+// One entry of the stability Hessian, H_ij = (sqrt(W_i) / sum W) sqrt(W_j)
+// J_ij, plus 1 + gt_i / 2 on the diagonal; explicit, so that the one-lane
+// and the several-lanes-per-run evaluations round alike.
+__device__ __forceinline__ double stab_hs(bool diag, double ri, double sWj, double Jij, double gti) {
+    const double rj = mul_rn<double>(ri, sWj);
+    return diag ? fma(rj, Jij, fma(0.5, gti, 1.0)) : mul_rn<double>(rj, Jij);
+}
+
 // sWin (optional): sqrt(W_i) of the point, when the caller has it (a trust-
 // region trial point beta + u gives it without an exponential); else from
 // ln W.  W = sqrt(W)^2, so no square root is taken either way.
@@ -845,8 +854,8 @@ __device__ __forceinline__ bool stab_point(const Comp<NC>& cp, const Mix<NC>& mx
 #pragma unroll
     for (int i = 0; i < NC; i++) {
         sW[i] = sWin ? sWin[i] : exp_fast(0.5 * p.lnW[i]);
-        W[i] = sW[i] * sW[i];
-        Wt += W[i];
+        W[i] = mul_rn<double>(sW[i], sW[i]);
+        Wt = add_rn<double>(Wt, W[i]);
     }
     const double inv = 1.0 / Wt;
 #pragma unroll
@@ -870,8 +879,7 @@ __device__ __forceinline__ bool stab_point(const Comp<NC>& cp, const Mix<NC>& mx
     for (int i = 0; i < NC; i++) {
         const double ri = sW[i] * inv;
 #pragma unroll
-        for (int j = 0; j <= i; j++)
-            p.H[tri(i, j)] = ri * sW[j] * J[tri(i, j)] + (i == j ? 1.0 + 0.5 * p.gt[i] : 0.0);
+        for (int j = 0; j <= i; j++) p.H[tri(i, j)] = stab_hs(i == j, ri, sW[j], J[tri(i, j)], p.gt[i]);
     }
     return true;
 }
@@ -998,18 +1006,309 @@ struct StabTR {
     }
 };
 
+// ---------------------------------------------------------------------------
+// The stability trust region with G lanes per run (lane r: component r):
+// StabTR::step operation for operation (the whole shift iteration in one
+// trip, as StabTR does once its queue has drained).
+// ---------------------------------------------------------------------------
+template <int NC, int G>
+struct StabTRG {
+    static constexpr int kHead = H_STAB_TR;
+    int64_t m, item;
+    int t, it, iters, phase, idle;
+    int32_t fl;
+    double kkr[NC];                 // row r of 1 - k_ij
+    double sA, Bi, d, beta;         // component r
+    double radius, eta_lo;
+    TRShift sh;
+    double lnW, gt, g, tm;          // current point: component r, and tm
+    double H[NC];                   // row r of the Hessian
+
+    template <class CS>
+    __device__ __forceinline__ void load_kk(const Grp& gr, const CS& cs) {
+        const Comp<NC>& cp = cs.of(m);
+        const int rr = gr.r < NC ? gr.r : 0;
+#pragma unroll
+        for (int j = 0; j < NC; j++) kkr[j] = cp.kk[rr * NC + j];
+    }
+
+    // a fresh run: queue position pos (as StabTR::begin)
+    template <class CS>
+    __device__ __forceinline__ void begin_pos(const Grp& gr, const CS& cs, const WS& ws, const IO&, int64_t pos) {
+        const int64_t n = ws.n;
+        const int rr = gr.r < NC ? gr.r : 0;
+        item = ws.q_stab_tr[pos];
+        m = ws.q_stab[item >> 1];
+        t = (int)(item & 1);
+        load_kk(gr, cs);
+        sA = ws.sA[rr * n + m];
+        Bi = ws.B[rr * n + m];
+        d = ws.d[rr * n + m];
+        lnW = ws.lnW[(t * NC + rr) * n + m];
+        fl = ws.tflag[t * n + m];
+        it = iters = phase = idle = 0;
+        radius = -1.0;
+        eta_lo = 0.0;
+        sh.active = 0;
+    }
+
+    // the run that lane src of the warp holds in its one-lane state s
+    // (every lane of the warp calls this: full-warp shuffles)
+    __device__ __forceinline__ void take_state(const Grp& gr, const StabTR<NC>& s, int src) {
+        constexpr unsigned F = 0xffffffffu;
+        const int rr = gr.r < NC ? gr.r : 0;
+        m = __shfl_sync(F, s.m, src);
+        item = __shfl_sync(F, s.item, src);
+        t = __shfl_sync(F, s.t, src);
+        it = __shfl_sync(F, s.it, src);
+        iters = __shfl_sync(F, s.iters, src);
+        phase = __shfl_sync(F, s.phase, src);
+        idle = __shfl_sync(F, s.idle, src);
+        fl = __shfl_sync(F, s.fl, src);
+        radius = __shfl_sync(F, s.radius, src);
+        eta_lo = __shfl_sync(F, s.eta_lo, src);
+        sh.eta = __shfl_sync(F, s.sh.eta, src);
+        sh.elo = __shfl_sync(F, s.sh.elo, src);
+        sh.ehi = __shfl_sync(F, s.sh.ehi, src);
+        sh.active = __shfl_sync(F, s.sh.active, src);
+        sh.it = __shfl_sync(F, s.sh.it, src);
+        tm = __shfl_sync(F, s.cur.tm, src);
+#pragma unroll
+        for (int k = 0; k < NC; k++) {
+            const double a1 = __shfl_sync(F, s.mx.sA[k], src), a2 = __shfl_sync(F, s.mx.B[k], src);
+            const double a3 = __shfl_sync(F, s.d[k], src), a4 = __shfl_sync(F, s.beta[k], src);
+            const double a5 = __shfl_sync(F, s.cur.lnW[k], src), a6 = __shfl_sync(F, s.cur.gt[k], src);
+            const double a7 = __shfl_sync(F, s.cur.g[k], src);
+            if (rr == k) {
+                sA = a1;
+                Bi = a2;
+                d = a3;
+                beta = a4;
+                lnW = a5;
+                gt = a6;
+                g = a7;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+#pragma unroll
+            for (int j = 0; j <= i; j++) {
+                const double v = __shfl_sync(F, s.cur.H[tri(i, j)], src);
+                if (rr == i) H[j] = v;
+                if (rr == j) H[i] = v;
+            }
+        }
+    }
+
+    // as StabTR::store
+    __device__ __forceinline__ void store(const Grp& gr, const WS& ws, int maxiter, int nonfinite) {
+        const int64_t n = ws.n;
+        if (gr.r < NC) ws.lnW[(t * NC + gr.r) * n + m] = lnW;
+        if (gr.r == 0) {
+            ws.tm[t * n + m] = nonfinite ? NAN : tm;
+            ws.tflag[t * n + m] = (fl & 0xff) | (iters << 8) | (1 << 16) | (maxiter << 17) | (nonfinite << 18);
+        }
+    }
+
+    // as stab_point at component r's ln W_r (sWin: sqrt(W_r) when the caller has it)
+    struct Pt {
+        double lnW, gt, g, tm;
+        double H[NC];
+    };
+    __device__ __forceinline__ bool point(const Grp& gr, Pt& p, bool have_sW, double sWin) const {
+        const double sW = have_sW ? sWin : exp_fast(0.5 * p.lnW);
+        const double W = mul_rn<double>(sW, sW);
+        double Wt = 0.0;
+#pragma unroll
+        for (int i = 0; i < NC; i++) Wt = add_rn<double>(Wt, gat<G>(gr, W, i));
+        const double inv = 1.0 / Wt;
+        const double c = W * inv;
+        PhaseG ph;
+        eos_g<NC, G>(gr, kkr, sA, Bi, c, ph);
+        p.gt = p.lnW + ph.lnphi - d;
+        double tt = 1.0;
+#pragma unroll
+        for (int i = 0; i < NC; i++) tt = fma(gat<G>(gr, W, i), gat<G>(gr, p.gt, i) - 1.0, tt);
+        p.tm = tt;
+        if (!isfinite(tt)) return false;
+        double J[NC];
+        dlnphi_dn_g<NC, G>(gr, kkr, sA, Bi, ph, J);
+        p.g = sW * p.gt;
+        const double ri = sW * inv;
+#pragma unroll
+        for (int j = 0; j < NC; j++) {
+            const double sWj = gat<G>(gr, sW, j);
+            if (j <= gr.r) p.H[j] = stab_hs(j == gr.r, ri, sWj, J[j], p.gt);
+        }
+        sym_fill<NC, G>(gr, p.H);
+        return true;
+    }
+
+    // as StabTR::step with tail = true
+    template <class CS>
+    __device__ __forceinline__ int step(const Grp& gr, const CS&, const WS& ws, const IO&) {
+        Pt nxt;
+        double u = 0.0, sWn = 0.0, pred = 0.0;
+        if (phase == 0) {
+            nxt.lnW = lnW;
+        } else {
+            double a[NC];
+            int r = 0;
+#pragma unroll 1
+            for (int k = 0; k < kTRShiftCap + 2 && r == 0; k++)
+                r = tr_shift_step_g<NC, G>(gr, H, g, radius, eta_lo, false, sh, a, u);
+            if (r == 0) {
+                if (++idle > (ws.ctl.tr_stab + 2) * (kTRShiftCap + 3)) {
+                    store(gr, ws, 1, 0);
+                    return 1;
+                }
+                return 0;
+            }
+            if (r < 0) {
+                store(gr, ws, 1, 0);
+                return 1;
+            }
+            double hd = 0.0;
+#pragma unroll
+            for (int j = 0; j < NC; j++) hd = fma(H[j], gat<G>(gr, u, j), hd);
+#pragma unroll
+            for (int i = 0; i < NC; i++) {
+                const double ui = gat<G>(gr, u, i);
+                pred = fma(gat<G>(gr, g, i), ui, fma(0.5 * ui, gat<G>(gr, hd, i), pred));
+            }
+            sWn = 0.5 * fabs(beta + u);
+            nxt.lnW = 2.0 * log_fast(sWn);
+        }
+        const bool ok = point(gr, nxt, phase != 0, sWn);
+        if (phase == 0) {
+            if (!ok) {
+                store(gr, ws, 0, 1);
+                return 1;
+            }
+            lnW = nxt.lnW;
+            gt = nxt.gt;
+            g = nxt.g;
+            tm = nxt.tm;
+#pragma unroll
+            for (int j = 0; j < NC; j++) H[j] = nxt.H[j];
+            beta = 2.0 * exp_fast(0.5 * lnW);
+            phase = 1;
+        } else {
+            const bool trusted = fabs(pred) > kPredTrust * (1.0 + fabs(tm));
+            const double rho = !ok ? -1.0 : (trusted ? (nxt.tm - tm) / pred : 0.5);
+            if (rho > 0.0) {
+                beta = fabs(beta + u);
+                lnW = nxt.lnW;
+                gt = nxt.gt;
+                g = nxt.g;
+                tm = nxt.tm;
+#pragma unroll
+                for (int j = 0; j < NC; j++) H[j] = nxt.H[j];
+                eta_lo = 0.0;
+            } else {
+                eta_lo = sh.eta;
+            }
+            if (rho <= 0.25) radius *= 0.5;
+            else if (rho >= 0.75) radius *= 2.0;
+            iters = ++it;
+        }
+        if (tm < -kEpsNeg || gmaxabs<NC, G>(gr, g) < ws.ctl.tol_stab) {
+            store(gr, ws, 0, 0);
+            return 1;
+        }
+        if (it >= ws.ctl.tr_stab) {
+            store(gr, ws, 1, 0);
+            return 1;
+        }
+        return 0;
+    }
+};
+
+// Trust-region runs with G lanes each (RunG: SplitTRG or StabTRG; Run: the
+// one-lane state of the same kind).  `pending` lists the warp's lanes whose
+// runs are still to be taken: each group that has no run takes the next of
+// them (lowest lane first), the rest stay parked in their lanes until a
+// group is free.  With refill, a free group takes the next run of the queue
+// instead.  Every lane of the warp calls this.
+template <class RunG, int G, class Run, class CS>
+__device__ __forceinline__ void tr_groups(const CS& cs, const WS& ws, const IO& io, const Run& s, unsigned pending,
+                                          bool refill, int64_t len) {
+    constexpr unsigned F = 0xffffffffu;
+    const Grp g = make_grp<G>();
+    const int lane = threadIdx.x & 31, q = lane / G;
+    RunG t;
+    bool ghave = false, gdrained = !refill;
+    for (;;) {
+        const unsigned idle = __ballot_sync(F, !ghave && g.r == 0);  // leader lanes of the free groups
+        if (pending && idle) {
+            // the k-th free group (by lane) takes the k-th lowest pending lane's run
+            const bool free = (idle >> (q * G)) & 1u;
+            const int k = __popc(idle & ((1u << (q * G)) - 1u));
+            unsigned pm = pending;
+            for (int i = 0; i < k && pm; i++) pm &= pm - 1;
+            const bool gets = free && pm != 0;
+            const int src = gets ? __ffs(pm) - 1 : lane;
+            RunG tk;
+            tk.take_state(g, s, src);  // full-warp shuffles
+            if (gets) {
+                t = tk;
+                t.load_kk(g, cs);
+                ghave = true;
+            }
+            const int taken = min(__popc(idle), __popc(pending));
+            for (int i = 0; i < taken; i++) pending &= pending - 1;
+        }
+        if (!ghave && !gdrained) {
+            int pos = 0;
+            if (g.r == 0) pos = atomicAdd(ws.cnt + RunG::kHead, 1);
+            pos = __shfl_sync(g.mask, pos, 0, G);
+            if (pos < len) {
+                t.begin_pos(g, cs, ws, io, pos);
+                ghave = true;
+            } else {
+                gdrained = true;
+            }
+        }
+        if (!__any_sync(F, ghave) && !pending) break;
+        if (ghave && t.step(g, cs, ws, io)) ghave = false;
+    }
+}
+
+// One lane per run while the queue lasts; once this warp's fetch has found
+// it drained and at most kGroupSwitch runs are left, G lanes per run, 32 / G
+// runs at a time (same results, shorter trips: see ptf_group.cuh).
+// ws.ctl.tr_coop 1: one lane throughout; 2: G lanes throughout.  A group trip
+// takes about half as long as a one-lane trip but costs 1.6x its FP64 work
+// per run, so groups pay only once the queue has drained; switching at 8 runs
+// left measured best (4 and 16 within 0.3 ms of it, 32 slower).
+constexpr int kGroupSwitch = 8;
+
 template <int NC, class CS>
 __global__ void __launch_bounds__(128) k_stab_tr(const __grid_constant__ CS cs, WS ws, IO io) {
+    constexpr int G = GroupLanes<NC>::G;
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_STAB_TR);
     StabTR<NC> s;
     bool have = false, drained = false;
+    if constexpr (GroupLanes<NC>::ok) {
+        if (ws.ctl.tr_coop == 2) {
+            tr_groups<StabTRG<NC, G>, G>(cs, ws, io, s, 0u, true, len);
+            return;
+        }
+    }
     for (;;) {
         const int64_t pos = warp_fetch(ws.cnt + H_STAB_TR, !have, len, drained);
         if (pos >= 0) {
             s.begin(cs, ws, io, ws.q_stab_tr[pos]);
             have = true;
         }
-        if (!__any_sync(0xffffffffu, have)) break;
+        const unsigned live = __ballot_sync(0xffffffffu, have);
+        if (!live) break;
+        if constexpr (GroupLanes<NC>::ok) {
+            if (drained && ws.ctl.tr_coop == 0 && __popc(live) <= kGroupSwitch) {
+                tr_groups<StabTRG<NC, G>, G>(cs, ws, io, s, live, false, len);
+                break;
+            }
+        }
         if (have && s.step(cs, ws, io, drained)) have = false;
     }
 }
@@ -1461,6 +1760,18 @@ __device__ __forceinline__ bool split_eval(const Comp<NC>& cp, const Mix<NC>& mx
     return isfinite(G);
 }
 
+// One entry of S H S: h = theta J^L_ij + (1 - theta) J^V_ij - 1, then
+// w S_i S_j h, plus w on the diagonal (shared by the one-lane and the
+// several-lanes-per-run models, so both round alike).
+template <class R>
+__device__ __forceinline__ R split_h(R th, R th1, R jl, R jv) {
+    return sub_rn<R>(fma(th, jl, mul_rn<R>(th1, jv)), R(1));  // explicit: no context contracts it otherwise
+}
+template <class R>
+__device__ __forceinline__ double split_hs(bool diag, R wSi, R Si, R Sj, R h, double w) {
+    return diag ? fma((double)mul_rn<R>(wSi, Si), (double)h, w) : (double)mul_rn<R>(mul_rn<R>(wSi, Sj), h);
+}
+
 // The trust region's model at an evaluated point: the scaled Hessian
 // S H S (Eq. split_hess, reading R5) from both phases' n_T d ln phi / dn,
 // formed in R.  The diagonal term z_i / (x_i y_i) of H scales to exactly 1.
@@ -1473,11 +1784,11 @@ __device__ __forceinline__ void split_model(const Comp<NC>& cp, const Mix<NC>& m
     const R th = (R)p.th, th1 = (R)(1.0 - p.th);
 #pragma unroll
     for (int i = 0; i < NC; i++) {
-        const R wSi = (R)(w * p.S[i]);
+        const R wSi = (R)mul_rn<double>(w, p.S[i]);
 #pragma unroll
         for (int j = 0; j <= i; j++) {
-            const R h = th * JL[tri(i, j)] + th1 * JV[tri(i, j)] - R(1);
-            p.Hs[tri(i, j)] = (i == j) ? fma((double)(wSi * (R)p.S[i]), (double)h, w) : (double)(wSi * (R)p.S[j] * h);
+            const R h = split_h<R>(th, th1, JL[tri(i, j)], JV[tri(i, j)]);
+            p.Hs[tri(i, j)] = split_hs<R>(i == j, wSi, (R)p.S[i], (R)p.S[j], h, w);
         }
     }
 }
@@ -1655,6 +1966,311 @@ struct SplitTR {
     }
 };
 
+// ---------------------------------------------------------------------------
+// The split trust region with G lanes per run (lane r: component r), used
+// once the queue has drained: SplitTR::step operation for operation, so the
+// results are the same bit for bit (see ptf_group.cuh).
+// ---------------------------------------------------------------------------
+template <int NC>
+struct PtG {
+    double th, G, ZL, ZV;   // scalars (the same on every lane of the group)
+    double x, y, gt, gs, S;  // component r
+    double H[NC];            // row r of S H S
+};
+
+template <int NC, int G>
+struct SplitTRG {
+    static constexpr int kHead = H_SPLIT_TR;
+    int64_t m;
+    int it, iters, newton_steps, phase, trips;
+    int32_t st;
+    double kkr[NC];                // row r of 1 - k_ij
+    double sA, Bi, z, iz, nV;      // component r
+    double radius, eta_lo;
+    TRShift sh;
+    PtG<NC> cur;
+
+    template <class CS>
+    __device__ __forceinline__ void load_kk(const Grp& g, const CS& cs) {
+        const Comp<NC>& cp = cs.of(m);
+        const int rr = g.r < NC ? g.r : 0;  // padding lanes copy component 0
+#pragma unroll
+        for (int j = 0; j < NC; j++) kkr[j] = cp.kk[rr * NC + j];
+    }
+
+    // a fresh run from the queue (as SplitTR::begin)
+    template <class CS>
+    __device__ __forceinline__ void begin(const Grp& g, const CS& cs, const WS& ws, const IO& io, int64_t mm) {
+        const int64_t n = ws.n;
+        const int rr = g.r < NC ? g.r : 0;
+        m = mm;
+        load_kk(g, cs);
+        sA = ws.sA[rr * n + m];
+        Bi = ws.B[rr * n + m];
+        z = io.z[rr * io.ld + m];
+        iz = 1.0 / z;
+        nV = ws.nV[rr * n + m];
+        st = io.status[m];
+        it = iters = newton_steps = phase = trips = 0;
+        radius = -1.0;
+        eta_lo = 0.0;
+        sh.active = 0;
+    }
+
+    // a fresh run: queue position pos (in the order k_tr_order laid out)
+    template <class CS>
+    __device__ __forceinline__ void begin_pos(const Grp& g, const CS& cs, const WS& ws, const IO& io, int64_t pos) {
+        begin(g, cs, ws, io, ws.q_sort[pos]);
+    }
+
+    // the run that lane src of the warp holds in its one-lane state s
+    // (every lane of the warp calls this: full-warp shuffles)
+    __device__ __forceinline__ void take_state(const Grp& g, const SplitTR<NC>& s, int src) {
+        constexpr unsigned F = 0xffffffffu;
+        const int rr = g.r < NC ? g.r : 0;
+        m = __shfl_sync(F, s.m, src);
+        it = __shfl_sync(F, s.it, src);
+        iters = __shfl_sync(F, s.iters, src);
+        newton_steps = __shfl_sync(F, s.newton_steps, src);
+        phase = __shfl_sync(F, s.phase, src);
+        trips = __shfl_sync(F, s.trips, src);
+        st = __shfl_sync(F, s.st, src);
+        radius = __shfl_sync(F, s.radius, src);
+        eta_lo = __shfl_sync(F, s.eta_lo, src);
+        sh.eta = __shfl_sync(F, s.sh.eta, src);
+        sh.elo = __shfl_sync(F, s.sh.elo, src);
+        sh.ehi = __shfl_sync(F, s.sh.ehi, src);
+        sh.active = __shfl_sync(F, s.sh.active, src);
+        sh.it = __shfl_sync(F, s.sh.it, src);
+        cur.th = __shfl_sync(F, s.cur.th, src);
+        cur.G = __shfl_sync(F, s.cur.G, src);
+        cur.ZL = __shfl_sync(F, s.cur.ZL, src);
+        cur.ZV = __shfl_sync(F, s.cur.ZV, src);
+#pragma unroll
+        for (int k = 0; k < NC; k++) {
+            const double a1 = __shfl_sync(F, s.mx.sA[k], src), a2 = __shfl_sync(F, s.mx.B[k], src);
+            const double a3 = __shfl_sync(F, s.z[k], src), a4 = __shfl_sync(F, s.iz[k], src);
+            const double a5 = __shfl_sync(F, s.nV[k], src), a6 = __shfl_sync(F, s.cur.x[k], src);
+            const double a7 = __shfl_sync(F, s.cur.y[k], src), a8 = __shfl_sync(F, s.cur.gt[k], src);
+            const double a9 = __shfl_sync(F, s.cur.gs[k], src), a10 = __shfl_sync(F, s.cur.S[k], src);
+            if (rr == k) {
+                sA = a1;
+                Bi = a2;
+                z = a3;
+                iz = a4;
+                nV = a5;
+                cur.x = a6;
+                cur.y = a7;
+                cur.gt = a8;
+                cur.gs = a9;
+                cur.S = a10;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+#pragma unroll
+            for (int j = 0; j <= i; j++) {
+                const double v = __shfl_sync(F, s.cur.Hs[tri(i, j)], src);
+                if (rr == i) cur.H[j] = v;
+                if (rr == j) cur.H[i] = v;
+            }
+        }
+    }
+
+    __device__ __forceinline__ void write_single_g(const Grp& g, const IO& io) {
+        const int64_t n = io.ld;
+        if (g.r == 0) {
+            io.nphase[m] = 1;
+            io.beta[m] = 0.0;
+        }
+        if (g.r < NC) {
+            io.x[g.r * n + m] = z;
+            io.y[g.r * n + m] = z;
+            io.K[g.r * n + m] = 1.0;
+        }
+    }
+
+    // as SplitTR::finish
+    __device__ __forceinline__ int finish(const Grp& g, const IO& io, int kind) {
+        if (kind == 1) {
+            st |= ST_NONFINITE;
+            write_single_g(g, io);
+        } else if (kind == 2) {
+            st |= ST_COLLAPSE | ST_MAXITER;
+            write_single_g(g, io);
+        } else if (!(cur.th > 0.0 && cur.th < 1.0)) {
+            st |= ST_COLLAPSE;
+            write_single_g(g, io);
+        } else {
+            const int64_t n = io.ld;
+            const bool swap = cur.ZV < cur.ZL;
+            if (g.r == 0) {
+                io.nphase[m] = 2;
+                io.beta[m] = swap ? 1.0 - cur.th : cur.th;
+            }
+            if (g.r < NC) {
+                const double xi = swap ? cur.y : cur.x, yi = swap ? cur.x : cur.y;
+                io.x[g.r * n + m] = xi;
+                io.y[g.r * n + m] = yi;
+                io.K[g.r * n + m] = yi / xi;
+            }
+        }
+        if (g.r == 0) {
+            io.status[m] = st;
+            if (io.iters) io.iters[m] = (io.iters[m] & ~0xff00) | ((iters & 0xff) << 8);
+        }
+        return 1;
+    }
+
+    // as split_eval, component r's vapour moles nv
+    __device__ __forceinline__ bool eval(const Grp& g, double nv, PtG<NC>& p, PhaseG& pl, PhaseG& pv, double& w) {
+        double th = 0.0;
+#pragma unroll
+        for (int i = 0; i < NC; i++) th += gat<G>(g, nv, i);
+        p.th = th;
+        w = 1.0 / (th * (1.0 - th));
+        const double iv = w * (1.0 - th), il = w * th;
+        p.y = nv * iv;
+        p.x = (z - nv) * il;
+        eos_g<NC, G>(g, kkr, sA, Bi, p.x, pl);
+        eos_g<NC, G>(g, kkr, sA, Bi, p.y, pv);
+        p.ZL = pl.Z;
+        p.ZV = pv.Z;
+        const double mul = log_fast(p.x) + pl.lnphi, muv = log_fast(p.y) + pv.lnphi;
+        p.gt = muv - mul;
+        const double zn = z - nv;
+        double Gs = 0.0;
+#pragma unroll
+        for (int i = 0; i < NC; i++)
+            Gs = fma(gat<G>(g, zn, i), gat<G>(g, mul, i), fma(gat<G>(g, nv, i), gat<G>(g, muv, i), Gs));
+        p.G = Gs;
+        p.S = sqrt(p.x * p.y * iz);
+        p.gs = p.S * p.gt;
+        return isfinite(Gs);
+    }
+
+    // as split_model (FP64)
+    __device__ __forceinline__ void model(const Grp& g, const PhaseG& pl, const PhaseG& pv, double w, PtG<NC>& p) {
+        double JL[NC], JV[NC];
+        dlnphi_dn_g<NC, G>(g, kkr, sA, Bi, pl, JL);
+        dlnphi_dn_g<NC, G>(g, kkr, sA, Bi, pv, JV);
+        const double th = p.th, th1 = 1.0 - p.th;
+        const double wSi = mul_rn<double>(w, p.S);
+#pragma unroll
+        for (int j = 0; j < NC; j++) {
+            const double Sj = gat<G>(g, p.S, j);
+            if (j <= g.r) {
+                const double h = split_h<double>(th, th1, JL[j], JV[j]);
+                p.H[j] = split_hs<double>(j == g.r, wSi, p.S, Sj, h, w);
+            }
+        }
+        sym_fill<NC, G>(g, p.H);
+    }
+
+    // as boundary_cut, component r's step d
+    __device__ __forceinline__ double boundary_cut_g(const Grp& g, double d) const {
+        const double a = d < 0.0 ? 0.99 * nV : 0.99 * (z - nV);
+        const double b = fabs(d);
+        double num = 1.0, den = 1.0;
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            const double ai = gat<G>(g, a, i), bi = gat<G>(g, b, i);
+            if (bi > 0.0 && ai * den < num * bi) {
+                num = ai;
+                den = bi;
+            }
+        }
+        return num == den ? 1.0 : num / den;
+    }
+
+    // as SplitTR::step
+    template <class CS>
+    __device__ __forceinline__ int step(const Grp& g, const CS& cs, const WS& ws, const IO& io) {
+        if (++trips > ws.ctl.tr_split + ws.ctl.polish + 8) {
+            st |= ST_MAXITER;
+            return finish(g, io, 0);
+        }
+        double u = 0.0, trial, pred = 0.0;
+        if (phase == 0) {
+            trial = nV;
+        } else {
+            double a[NC];
+            int r = 0;
+#pragma unroll 1
+            for (int k = 0; k < kTRShiftCap + 2 && r == 0; k++)
+                r = tr_shift_step_g<NC, G>(g, cur.H, cur.gs, radius, eta_lo, phase == 2, sh, a, u);
+            if (r == 0) return 0;
+            if (r < 0) {
+                if (phase == 1 || gmaxabs<NC, G>(g, cur.gt) > ws.ctl.tol_fug) st |= ST_MAXITER;
+                return finish(g, io, 0);
+            }
+            double dstep = cur.S * u;
+            const double tau = boundary_cut_g(g, dstep);
+            if (tau < 1.0) {
+                u *= tau;
+                dstep *= tau;
+            }
+            if (phase == 1) {
+                double hd = 0.0;
+#pragma unroll
+                for (int j = 0; j < NC; j++) hd = fma(cur.H[j], gat<G>(g, u, j), hd);
+#pragma unroll
+                for (int i = 0; i < NC; i++) {
+                    const double ui = gat<G>(g, u, i);
+                    pred = fma(gat<G>(g, cur.gs, i), ui, fma(0.5 * ui, gat<G>(g, hd, i), pred));
+                }
+            }
+            trial = nV + dstep;
+        }
+        PtG<NC> nxt;
+        bool ok;
+        {
+            PhaseG pl, pv;
+            double w;
+            ok = eval(g, trial, nxt, pl, pv, w);
+            if (ok) model(g, pl, pv, w, nxt);
+        }
+        if (phase == 0) {
+            if (!ok) return finish(g, io, 1);
+            cur = nxt;
+            phase = 1;
+        } else if (phase == 2) {
+            if (!ok) return finish(g, io, 1);
+            nV = trial;
+            cur = nxt;
+            newton_steps++;
+            iters++;
+        } else {
+            const bool trusted = fabs(pred) > kPredTrust * (1.0 + fabs(cur.G));
+            const double rho = !ok ? -1.0 : (trusted ? (nxt.G - cur.G) / pred : 0.5);
+            if (rho > 0.0) {
+                nV = trial;
+                cur = nxt;
+                eta_lo = 0.0;
+            } else {
+                eta_lo = sh.eta;
+            }
+            if (rho <= 0.25) radius *= 0.5;
+            else if (rho >= 0.75) radius *= 2.0;
+            iters = ++it;
+        }
+        if (!(cur.th > kCollapseTheta && cur.th < 1.0 - kCollapseTheta)) return finish(g, io, 2);
+        const double res = gmaxabs<NC, G>(g, cur.gt);
+        if (phase == 1 && res < ws.ctl.tol_split_tr) phase = 2;
+        if (phase == 2) {
+            if (res <= ws.ctl.tol_fug && newton_steps >= 1) return finish(g, io, 0);
+            if (newton_steps >= ws.ctl.polish) {
+                st |= ST_MAXITER;
+                return finish(g, io, 0);
+            }
+        } else if (it >= ((st & ST_NN_INIT) ? min(ws.ctl.tr_split, kTRStab) : ws.ctl.tr_split)) {
+            st |= ST_MAXITER;
+            return finish(g, io, 0);
+        }
+        return 0;
+    }
+};
+
 // Lay the split trust-region queue out by bucket (longest expected runs
 // first) into ws.q_sort: each block forms the bucket offsets from the counts,
 // and the items of a bucket take consecutive positions from its cursor.
@@ -1676,18 +2292,32 @@ static __global__ void __launch_bounds__(128) k_tr_order(WS ws) {
     }
 }
 
+// As k_stab_tr: one lane per run while the queue lasts, then G lanes per run.
 template <int NC, class CS>
 __global__ void __launch_bounds__(128, 3) k_split_tr(const __grid_constant__ CS cs, WS ws, IO io) {
     const int64_t len = *(volatile int32_t*)(ws.cnt + Q_SPLIT_TR);
     SplitTR<NC> s;
     bool have = false, drained = false;
+    if constexpr (GroupLanes<NC>::ok) {
+        if (ws.ctl.tr_coop == 2) {
+            tr_groups<SplitTRG<NC, GroupLanes<NC>::G>, GroupLanes<NC>::G>(cs, ws, io, s, 0u, true, len);
+            return;
+        }
+    }
     for (;;) {
         const int64_t pos = warp_fetch(ws.cnt + H_SPLIT_TR, !have, len, drained);
         if (pos >= 0) {
             s.begin(cs, ws, io, ws.q_sort[pos]);  // in the order k_tr_order laid out
             have = true;
         }
-        if (!__any_sync(0xffffffffu, have)) break;
+        const unsigned live = __ballot_sync(0xffffffffu, have);
+        if (!live) break;
+        if constexpr (GroupLanes<NC>::ok) {
+            if (drained && ws.ctl.tr_coop == 0 && __popc(live) <= kGroupSwitch) {
+                tr_groups<SplitTRG<NC, GroupLanes<NC>::G>, GroupLanes<NC>::G>(cs, ws, io, s, live, false, len);
+                break;
+            }
+        }
         if (have && s.step(cs, ws, io)) have = false;
     }
 }

@@ -43,12 +43,12 @@ class ptflash_options(ctypes.Structure):
                 ("max_ss_stab", ctypes.c_int32), ("max_tr_stab", ctypes.c_int32), ("max_ss_split", ctypes.c_int32),
                 ("max_tr_split", ctypes.c_int32), ("max_polish", ctypes.c_int32), ("tol_stab", ctypes.c_double),
                 ("tol_split_tr", ctypes.c_double), ("tol_fug", ctypes.c_double), ("nn_lnk_dev", ctypes.c_double),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("tr_lanes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 # ptflash_options fields a caller may set through **opts (0 = default)
 OPTION_FIELDS = ("max_ss_stab", "max_tr_stab", "max_ss_split", "max_tr_split", "max_polish", "tol_stab",
-                 "tol_split_tr", "tol_fug", "nn_lnk_dev")
+                 "tol_split_tr", "tol_fug", "nn_lnk_dev", "tr_lanes")
 
 
 def load(path: str = LIB_PATH):

@@ -86,5 +86,6 @@ def test_default_options_without_gpu():
     assert d["max_ss_split"] == 9 and d["max_tr_split"] == 60 and d["max_polish"] == 10
     assert d["tol_stab"] == 1e-6 and d["tol_split_tr"] == 1e-8 and d["tol_fug"] == 0.98e-10
     assert d["p_l"] == 0.02 and d["p_r"] == 0.98 and d["nn_lnk_dev"] == 0.3
+    assert d["tr_lanes"] == 0  # one lane per trust-region run, several in the drain
     assert ctypes.sizeof(ptflash.ptflash_options) == 88  # the C sizeof on LP64 (x86-64 and aarch64)
     assert ptflash.load().ptflash_default_options(None) == -1
