@@ -1231,7 +1231,7 @@ struct StabTRG {
 // group is free.  With refill, a free group takes the next run of the queue
 // instead.  Every lane of the warp calls this.
 template <class RunG, int G, class Run, class CS>
-__device__ __forceinline__ void tr_groups(const CS& cs, const WS& ws, const IO& io, const Run& s, unsigned pending,
+__device__ __noinline__ void tr_groups(const CS& cs, const WS& ws, const IO& io, const Run& s, unsigned pending,
                                           bool refill, int64_t len) {
     constexpr unsigned F = 0xffffffffu;
     const Grp g = make_grp<G>();
