@@ -237,7 +237,7 @@ __device__ __forceinline__ double shift_bound_g(const Grp& g, const double* a, i
 template <int NC, int G>
 __device__ __forceinline__ int tr_shift_step_g(const Grp& g, const double* H, double gs, double& radius, double eta_lo,
                                                bool newton_only, TRShift& sh, double* a, double& u) {
-    constexpr double kShiftTol = 1e-10;
+    constexpr double kShiftTol = 1e-4;
     constexpr double kPoleTol = 1e-12;
     if (sh.active && sh.it > kTRShiftCap + 2) {
         sh.active = 0;
