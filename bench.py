@@ -595,9 +595,10 @@ def ours_arm(args, ws, rank, local):
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "traffic_source": traffic_src,
-                     "peak_source": f"152 SMs x 2 FP64 FMA/clk x 2 flop x {sm_mhz:.0f} MHz (sampled median); "
-                                    f"the FP64 FMA probe (ptflash_fp64_fma_rate) measured {probe_tf:.3f} TFLOP/s "
-                                    f"on this GPU after the timed steps",
+                     "peak_source": f"152 SMs x 2 FP64 FMA/clk x 2 flop x {sm_mhz:.0f} MHz (sampled median), "
+                                    f"the unit-count peak (MEASURED_PEAKS.json has no FP64 figure); the FP64 FMA "
+                                    f"probe (ptflash_fp64_fma_rate, profiles/fp64_fma_probe.md) measured "
+                                    f"{probe_tf:.3f} TFLOP/s on this GPU after the timed steps: frac_of_probe",
                      "peak_probe": probe_tf, "frac_of_probe": (achieved / probe_tf) if achieved else None,
                      "fp64_ops": work, "transcendental_ops": special,
                      "ops_note": "oracle-counted algorithmic work of the dominant stage per launch: fp64_ops are "

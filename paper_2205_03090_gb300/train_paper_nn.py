@@ -10,8 +10,8 @@ case.
     python -m paper_2205_03090_gb300.train_paper_nn [--n 1000000] [--epochs 30] [--stage2-epochs 4]
         [--patience 6] [--out PATH]
 
-The committed checkpoint was trained with --n 2700000 --epochs 60
---stage2-epochs 10 --patience 8: about 1e6 of the 2.7e6 mixtures are two-phase,
+The committed checkpoint was trained with --n 2700000 --epochs 150
+--stage2-epochs 10 --patience 20: about 1e6 of the 2.7e6 mixtures are two-phase,
 the size of the paper's initializer set (Sec. 4.2.2).
 """
 from __future__ import annotations
