@@ -25,6 +25,9 @@ Comp<NC> make_comp(const CompHost& h) {
         c.lnPc[i] = std::log(h.Pc[i]);
         c.mi[i] = 0.480 + 1.574 * h.om[i] - 0.176 * h.om[i] * h.om[i];
         c.wc[i] = kWilson * (1.0 + h.om[i]);
+        c.rsTc[i] = 1.0 / std::sqrt(h.Tc[i]);
+        c.sOmA[i] = std::sqrt(kOmegaA / h.Pc[i]);
+        c.OmB[i] = kOmegaB / h.Pc[i];
     }
     return c;
 }

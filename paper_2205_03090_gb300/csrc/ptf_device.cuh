@@ -86,6 +86,7 @@ template <int NC>
 struct Comp {
     double kk[NC * NC];  // 1 - k_ij
     double Tc[NC], Pc[NC], lnPc[NC], mi[NC], wc[NC];  // wc = 5.373 (1 + omega)
+    double rsTc[NC], sOmA[NC], OmB[NC];  // 1 / sqrt(Tc), sqrt(0.42748 / Pc), 0.08664 / Pc
     float kkf[NC * NC];  // 1 - k_ij in FP32 (the FP32 stability pre-iteration)
 };
 
@@ -164,18 +165,19 @@ struct Mix {
 
 // Appendix A: A_i = 0.42748 alpha_i (P/Pc)(Tc/T)^2, B_i = 0.08664 (P/Pc)(Tc/T),
 // alpha_i = [1 + m_i (1 - sqrt(T/Tc))]^2.
+// The component factors 1/sqrt(Tc_i), sqrt(0.42748/Pc_i) and 0.08664/Pc_i are
+// in the table, so a mixture takes one division and two square roots for all
+// its components: sqrt(A_i) = sqrt(0.42748/Pc_i) sqrt(P) |a_i| Tc_i / T with
+// a_i = 1 + m_i (1 - sqrt(T) / sqrt(Tc_i)), and B_i = (0.08664/Pc_i) P Tc_i / T.
 template <int NC>
 __device__ __forceinline__ void mix_init(const Comp<NC>& cp, double P, double T, Mix<NC>& mx) {
-    double invT = 1.0 / T;
+    const double invT = 1.0 / T, sT = sqrt(T);
+    const double sPT = sqrt(P) * invT, PT = P * invT;
 #pragma unroll
     for (int i = 0; i < NC; i++) {
-        double tr = T / cp.Tc[i];
-        double a = 1.0 + cp.mi[i] * (1.0 - sqrt(tr));
-        double pr = P / cp.Pc[i];
-        double trinv = cp.Tc[i] * invT;
-        // sqrt(A_i) = sqrt(0.42748 pr) |a| trinv
-        mx.sA[i] = sqrt(kOmegaA * pr) * fabs(a) * trinv;
-        mx.B[i] = kOmegaB * pr * trinv;
+        const double a = fma(cp.mi[i], fma(-sT, cp.rsTc[i], 1.0), 1.0);
+        mx.sA[i] = cp.sOmA[i] * sPT * fabs(a) * cp.Tc[i];
+        mx.B[i] = cp.OmB[i] * PT * cp.Tc[i];
     }
 }
 
