@@ -371,21 +371,27 @@ struct PrecheckSS {
         }
         eos<NC>(cp, mx, x, pl);
         eos<NC>(cp, mx, y, pv);
+        if (++it < kPrecheck) {
 #pragma unroll
-        for (int i = 0; i < NC; i++) lnK[i] -= lnK[i] + pv.lnphi[i] - pl.lnphi[i];
-        if (++it < kPrecheck) return 0;
+            for (int i = 0; i < NC; i++) lnK[i] -= lnK[i] + pv.lnphi[i] - pl.lnphi[i];
+            return 0;
+        }
         // Eq. tpd for the current phases; Delta G = (1-theta) tpd(x) + theta tpd(y).
         // sx, sy: sum c_i |ln c_i + ln phi_i(c) - d_i|, the first-order size of a
-        // change of tpd per relative change of the phase compositions
+        // change of tpd per relative change of the phase compositions.  y = K x,
+        // so ln y = ln K + ln x with the ln K these phases came from (one
+        // logarithm per component instead of two).
         double tx = 0.0, ty = 0.0, sx = 0.0, sy = 0.0;
 #pragma unroll
         for (int i = 0; i < NC; i++) {
             const double d = ws.d[i * n + m];
-            const double gx = log_fast(x[i]) + pl.lnphi[i] - d, gy = log_fast(y[i]) + pv.lnphi[i] - d;
+            const double lx = log_fast(x[i]);
+            const double gx = lx + pl.lnphi[i] - d, gy = (lx + lnK[i]) + pv.lnphi[i] - d;
             tx = fma(x[i], gx, tx);
             ty = fma(y[i], gy, ty);
             sx = fma(x[i], fabs(gx), sx);
             sy = fma(y[i], fabs(gy), sy);
+            lnK[i] -= lnK[i] + pv.lnphi[i] - pl.lnphi[i];  // the next K (the split starts from it)
         }
         const double dG = (1.0 - th) * tx + th * ty;
         if (from32) {
