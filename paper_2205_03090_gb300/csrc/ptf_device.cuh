@@ -837,6 +837,12 @@ __device__ __forceinline__ void bwd(const R* Lf, R* b) {
 //    is concave), so the first starts from the eta = 0 factorisation, and a
 //    caller that shrank the radius around the same H passes the previous shift
 //    as a further lower bound.
+//  - warm start (More and Sorensen 1983, Sec. 4): a run whose previous solve
+//    ended on the boundary (sh.warm > 0, that solve's shift) starts the next
+//    one from that shift, inside the new bracket, instead of from eta = 0:
+//    the shift changes little from trip to trip.  If the step there falls
+//    short of the radius and nothing excludes eta = 0 (elo == 0), eta = 0 is
+//    tried next, where a Newton step that fits ends the solve.
 //  - the iteration also stops once the bracket has closed to 1e-12 relative
 //    (1e-6 in FP32): with the shift at the pole -lambda_min (the nearly hard
 //    case) ||u|| can change by 1e-8 relative for the smallest change of eta.
@@ -851,8 +857,31 @@ constexpr int kTRShiftCap = 40;
 
 struct TRShift {
     double eta, elo, ehi;
+    double warm;  // shift of the run's last boundary step (0: none yet, or an interior step)
     int active, it;
+    int zero;     // this solve has factored at eta = 0
 };
+
+// The shift bracket of a fresh solve: Gershgorin bounds of H and ||g|| / radius
+template <int NC>
+__device__ __forceinline__ void shift_bracket(const double* Hs, const double* gs, double radius, double eta_lo,
+                                              TRShift& sh) {
+    double gn = 0.0, hn1 = 0.0, mind = 1e300;
+#pragma unroll 1
+    for (int i = 0; i < NC; i++) {
+        gn = fma(gs[i], gs[i], gn);
+        double rs = 0.0;
+#pragma unroll 1
+        for (int j = 0; j < NC; j++) rs += fabs(Hs[i >= j ? tri(i, j) : tri(j, i)]);
+        hn1 = fmax(hn1, rs);
+        mind = fmin(mind, Hs[tri(i, i)]);
+    }
+    gn = sqrt(gn);
+    sh.elo = fmax(fmax(0.0, eta_lo), fmax(-mind, gn / radius - hn1));
+    sh.ehi = gn / radius + hn1;
+    sh.active = 1;
+    sh.it = 0;
+}
 
 template <int NC, class R>
 __device__ __forceinline__ int tr_shift_step(const double* Hs, const double* gs, double& radius, double eta_lo,
@@ -862,6 +891,11 @@ __device__ __forceinline__ int tr_shift_step(const double* Hs, const double* gs,
     if (sh.active && sh.it > kTRShiftCap + 2) {
         sh.active = 0;
         return -1;
+    }
+    if (!sh.active && !newton_only && sh.warm > 0.0 && radius > 0.0) {
+        shift_bracket<NC>(Hs, gs, radius, eta_lo, sh);
+        sh.zero = 0;
+        sh.eta = fmin(fmax(sh.warm, sh.elo), sh.ehi);
     }
     const double eta = sh.active ? sh.eta : 0.0;
     R dfail = R(0);
@@ -884,10 +918,17 @@ __device__ __forceinline__ int tr_shift_step(const double* Hs, const double* gs,
             if (radius <= 0.0) radius = un;
             if (un <= radius) {
                 sh.eta = 0.0;
+                sh.warm = 0.0;
                 return 1;
             }
+        } else if (eta == 0.0 && un <= radius) {  // a warm start back at eta = 0: the Newton step fits
+            sh.active = 0;
+            sh.eta = 0.0;
+            sh.warm = 0.0;
+            return 1;
         } else if (fabs(un - radius) <= kShiftTol * radius || sh.it >= kTRShiftCap) {
             sh.active = 0;
+            sh.warm = eta;
             return 1;
         }
     } else if (newton_only) {
@@ -895,21 +936,8 @@ __device__ __forceinline__ int tr_shift_step(const double* Hs, const double* gs,
     }
     if (!sh.active) {
         if (radius <= 0.0) radius = 1.0;
-        double gn = 0.0, hn1 = 0.0, mind = 1e300;
-#pragma unroll 1
-        for (int i = 0; i < NC; i++) {
-            gn = fma(gs[i], gs[i], gn);
-            double rs = 0.0;
-#pragma unroll 1
-            for (int j = 0; j < NC; j++) rs += fabs(Hs[i >= j ? tri(i, j) : tri(j, i)]);
-            hn1 = fmax(hn1, rs);
-            mind = fmin(mind, Hs[tri(i, i)]);
-        }
-        gn = sqrt(gn);
-        sh.elo = fmax(fmax(0.0, eta_lo), fmax(-mind, gn / radius - hn1));
-        sh.ehi = gn / radius + hn1;
-        sh.active = 1;
-        sh.it = 0;
+        shift_bracket<NC>(Hs, gs, radius, eta_lo, sh);
+        sh.zero = 1;
     }
     sh.it++;
     if (!pd) {
@@ -926,9 +954,15 @@ __device__ __forceinline__ int tr_shift_step(const double* Hs, const double* gs,
     // positive definite, ||u|| off the radius: Newton step on the secular equation
     if (un < radius) sh.ehi = eta;
     else sh.elo = fmax(sh.elo, eta);
+    if (un < radius && !sh.zero && sh.elo == 0.0) {  // warm start right of the root: eta = 0 first
+        sh.zero = 1;
+        sh.eta = 0.0;
+        return 0;
+    }
     if (sh.ehi - sh.elo <= kPoleTol * sh.ehi) {  // shift pinned at the pole: ||u|| is as close as it gets
         sh.active = 0;
         sh.eta = eta;
+        sh.warm = eta;
         return 1;
     }
     R q[NC];
@@ -946,6 +980,7 @@ __device__ __forceinline__ int tr_shift_step(const double* Hs, const double* gs,
     if (en == eta) {  // no representable progress: take this step
         sh.active = 0;
         sh.eta = eta;
+        sh.warm = eta;
         return 1;
     }
     sh.eta = en;

@@ -232,6 +232,29 @@ __device__ __forceinline__ double shift_bound_g(const Grp& g, const double* a, i
     return eta - d / wn;
 }
 
+// As shift_bracket, H and gs by rows (the same chains on every lane)
+template <int NC, int G>
+__device__ __forceinline__ void shift_bracket_g(const Grp& g, const double* H, double gs, double radius, double eta_lo,
+                                                TRShift& sh) {
+    double rs = 0.0;
+#pragma unroll
+    for (int j = 0; j < NC; j++) rs += fabs(H[j]);
+    const double hd = pick_row<NC>(H, g.r);
+    double gn = 0.0, hn1 = 0.0, mind = 1e300;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        const double gi = gat<G>(g, gs, i);
+        gn = fma(gi, gi, gn);
+        hn1 = fmax(hn1, gat<G>(g, rs, i));
+        mind = fmin(mind, gat<G>(g, hd, i));
+    }
+    gn = sqrt(gn);
+    sh.elo = fmax(fmax(0.0, eta_lo), fmax(-mind, gn / radius - hn1));
+    sh.ehi = gn / radius + hn1;
+    sh.active = 1;
+    sh.it = 0;
+}
+
 // The trust-region subproblem as `tr_shift_step` (FP64), with H, gs and u by
 // rows.  Every branch rests on values that are the same on every lane.
 template <int NC, int G>
@@ -242,6 +265,11 @@ __device__ __forceinline__ int tr_shift_step_g(const Grp& g, const double* H, do
     if (sh.active && sh.it > kTRShiftCap + 2) {
         sh.active = 0;
         return -1;
+    }
+    if (!sh.active && !newton_only && sh.warm > 0.0 && radius > 0.0) {
+        shift_bracket_g<NC, G>(g, H, gs, radius, eta_lo, sh);
+        sh.zero = 0;
+        sh.eta = fmin(fmax(sh.warm, sh.elo), sh.ehi);
     }
     const double eta = sh.active ? sh.eta : 0.0;
     double dfail = 0.0;
@@ -258,10 +286,17 @@ __device__ __forceinline__ int tr_shift_step_g(const Grp& g, const double* H, do
             if (radius <= 0.0) radius = un;
             if (un <= radius) {
                 sh.eta = 0.0;
+                sh.warm = 0.0;
                 return 1;
             }
+        } else if (eta == 0.0 && un <= radius) {
+            sh.active = 0;
+            sh.eta = 0.0;
+            sh.warm = 0.0;
+            return 1;
         } else if (fabs(un - radius) <= kShiftTol * radius || sh.it >= kTRShiftCap) {
             sh.active = 0;
+            sh.warm = eta;
             return 1;
         }
     } else if (newton_only) {
@@ -269,23 +304,8 @@ __device__ __forceinline__ int tr_shift_step_g(const Grp& g, const double* H, do
     }
     if (!sh.active) {
         if (radius <= 0.0) radius = 1.0;
-        double rs = 0.0;
-#pragma unroll
-        for (int j = 0; j < NC; j++) rs += fabs(H[j]);
-        const double hd = pick_row<NC>(H, g.r);
-        double gn = 0.0, hn1 = 0.0, mind = 1e300;
-#pragma unroll
-        for (int i = 0; i < NC; i++) {
-            const double gi = gat<G>(g, gs, i);
-            gn = fma(gi, gi, gn);
-            hn1 = fmax(hn1, gat<G>(g, rs, i));
-            mind = fmin(mind, gat<G>(g, hd, i));
-        }
-        gn = sqrt(gn);
-        sh.elo = fmax(fmax(0.0, eta_lo), fmax(-mind, gn / radius - hn1));
-        sh.ehi = gn / radius + hn1;
-        sh.active = 1;
-        sh.it = 0;
+        shift_bracket_g<NC, G>(g, H, gs, radius, eta_lo, sh);
+        sh.zero = 1;
     }
     sh.it++;
     if (!pd) {
@@ -298,9 +318,15 @@ __device__ __forceinline__ int tr_shift_step_g(const Grp& g, const double* H, do
     if (!(sh.ehi > sh.elo)) sh.ehi = 2.0 * sh.elo + 1e-300;
     if (un < radius) sh.ehi = eta;
     else sh.elo = fmax(sh.elo, eta);
+    if (un < radius && !sh.zero && sh.elo == 0.0) {
+        sh.zero = 1;
+        sh.eta = 0.0;
+        return 0;
+    }
     if (sh.ehi - sh.elo <= kPoleTol * sh.ehi) {
         sh.active = 0;
         sh.eta = eta;
+        sh.warm = eta;
         return 1;
     }
     const double q = fwd_g<NC, G>(g, a, ur);
@@ -313,6 +339,7 @@ __device__ __forceinline__ int tr_shift_step_g(const Grp& g, const double* H, do
     if (en == eta) {
         sh.active = 0;
         sh.eta = eta;
+        sh.warm = eta;
         return 1;
     }
     sh.eta = en;

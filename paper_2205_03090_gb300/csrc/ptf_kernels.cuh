@@ -922,6 +922,7 @@ struct StabTR {
         radius = -1.0;
         eta_lo = 0.0;
         sh.active = 0;
+        sh.warm = 0.0;
     }
 
     __device__ __forceinline__ void store(const WS& ws, int maxiter, int nonfinite) {
@@ -1056,6 +1057,7 @@ struct StabTRG {
         radius = -1.0;
         eta_lo = 0.0;
         sh.active = 0;
+        sh.warm = 0.0;
     }
 
     // the run that lane src of the warp holds in its one-lane state s
@@ -1078,6 +1080,8 @@ struct StabTRG {
         sh.ehi = __shfl_sync(F, s.sh.ehi, src);
         sh.active = __shfl_sync(F, s.sh.active, src);
         sh.it = __shfl_sync(F, s.sh.it, src);
+        sh.warm = __shfl_sync(F, s.sh.warm, src);
+        sh.zero = __shfl_sync(F, s.sh.zero, src);
         tm = __shfl_sync(F, s.cur.tm, src);
 #pragma unroll
         for (int k = 0; k < NC; k++) {
@@ -1848,6 +1852,7 @@ struct SplitTR {
         radius = -1.0;
         eta_lo = 0.0;
         sh.active = 0;
+        sh.warm = 0.0;
     }
 
     // kind 0 result, 1 non-finite, 2 collapsed onto one phase without converging
@@ -2021,6 +2026,7 @@ struct SplitTRG {
         radius = -1.0;
         eta_lo = 0.0;
         sh.active = 0;
+        sh.warm = 0.0;
     }
 
     // a fresh run: queue position pos (in the order k_tr_order laid out)
@@ -2048,6 +2054,8 @@ struct SplitTRG {
         sh.ehi = __shfl_sync(F, s.sh.ehi, src);
         sh.active = __shfl_sync(F, s.sh.active, src);
         sh.it = __shfl_sync(F, s.sh.it, src);
+        sh.warm = __shfl_sync(F, s.sh.warm, src);
+        sh.zero = __shfl_sync(F, s.sh.zero, src);
         cur.th = __shfl_sync(F, s.cur.th, src);
         cur.G = __shfl_sync(F, s.cur.G, src);
         cur.ZL = __shfl_sync(F, s.cur.ZL, src);
