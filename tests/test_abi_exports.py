@@ -4,6 +4,10 @@ import ctypes
 import glob
 import os
 import re
+import shutil
+import subprocess
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -89,3 +93,23 @@ def test_default_options_without_gpu():
     assert d["tr_lanes"] == 0  # one lane per trust-region run, several in the drain
     assert ctypes.sizeof(ptflash.ptflash_options) == 88  # the C sizeof on LP64 (x86-64 and aarch64)
     assert ptflash.load().ptflash_default_options(None) == -1
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs a host C compiler")
+def test_options_layout_matches_header(tmp_path):
+    """Every field of ptflash_options sits at the same offset in the C header
+    (compiled by the host C compiler) and in the binding's ctypes mirror, so a
+    field added on one side only is caught without a GPU."""
+    from paper_2205_03090_gb300 import ptflash
+    fields = [f for f, _ in ptflash.ptflash_options._fields_]
+    src = tmp_path / "layout.c"
+    body = "\n".join(f'    printf("%s %zu\\n", "{f}", offsetof(ptflash_options, {f}));' for f in fields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ptflash.h"\nint main(void) {\n'
+                   f'{body}\n    printf("sizeof %zu\\n", sizeof(ptflash_options));\n    return 0;\n}}\n')
+    exe = str(tmp_path / "layout")
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", exe], check=True)
+    out = dict(line.split() for line in subprocess.run([exe], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for f in fields:
+        assert int(out[f]) == getattr(ptflash.ptflash_options, f).offset, f
+    assert int(out["sizeof"]) == ctypes.sizeof(ptflash.ptflash_options)
